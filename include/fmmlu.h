@@ -1,0 +1,165 @@
+/*
+ * fmmlu.h -- C ABI of the GB300 FMM-LU library (recursive strong
+ * skeletonization of the 3-D Helmholtz combined-field integral equation).
+ *
+ * The system solved is the sqrt(w)-scaled Nystrom discretisation of
+ *     1/2 sigma + D sigma - i eta S sigma = f          (Sec. 3, Eq. disc3)
+ * with G(x,y) = exp(i k |x-y|)/(4 pi |x-y|) (Eq. greenfunhelm) and the
+ * combined-field kernel K(x,y) = n(y).grad_y G(x,y) - i eta G(x,y)
+ * (Eq. comb_ref):
+ *     A_ij = sqrt(w_i) K(x_i, x_j) sqrt(w_j)                     (i != j)
+ *     A_ii = 1/2 - i eta (sqrt(w_i/pi)/2 + i k w_i/(4 pi))
+ * The diagonal keeps the exterior jump 1/2, sets the double-layer self term
+ * to 0 and replaces the single-layer self term by the two-term expansion of
+ * the integral of G over a disc of area w_i. Right-hand sides are b = sqrt(w) f
+ * and solutions x = sqrt(w) sigma.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success, a negative FMMLU_ERR_* code otherwise; the message
+ *    of the last error of the calling thread is fmmlu_last_error(). No C++
+ *    exception crosses this boundary; kernels never trap, they report through
+ *    a device status word that the host turns into an error code.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory of
+ *    the current device; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). All work is
+ *    ordered on it; calls that return sizes or statistics synchronise it.
+ *  - Complex arrays are complex128, interleaved (re, im) doubles.
+ *  - Point arrays are N x 3 row-major doubles in the caller's order. The
+ *    library works in Morton order internally and permutes b and x itself.
+ *  - The library copies what it needs from input arrays during the call; the
+ *    caller keeps ownership of every array it passes. Handles own all their
+ *    device memory (tree, factors) until fmmlu_free.
+ */
+#ifndef FMMLU_H
+#define FMMLU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMMLU_OK 0
+#define FMMLU_ERR_INVALID_ARG -1  /* null pointer, n < 1, bad option value  */
+#define FMMLU_ERR_OOM -2          /* a device or host allocation failed     */
+#define FMMLU_ERR_CUDA -3         /* a CUDA runtime call failed             */
+#define FMMLU_ERR_SINGULAR_PIVOT -4 /* X_RR or a root block had a zero or
+                                       non-finite pivot (Sec. 4.1 assumes
+                                       X_RR invertible)                      */
+#define FMMLU_ERR_NONFINITE -5    /* NaN/Inf in inputs or in a computed ID   */
+#define FMMLU_ERR_DEPTH_CAP -6    /* a leaf at the 21-level depth cap holds
+                                     more than leaf_size points (warning
+                                     only: reported by fmmlu_stats)          */
+#define FMMLU_ERR_TIMEOUT -7      /* a bounded device wait gave up           */
+#define FMMLU_ERR_LIMIT -8        /* a size exceeds a documented maximum     */
+
+#define FMMLU_PRECISION_AUTO 0    /* mixed when eps >= 1e-5, else fp64       */
+#define FMMLU_PRECISION_FP64 1    /* everything complex128                   */
+#define FMMLU_PRECISION_MIXED 2   /* ID matrix assembly and pivoted QR in
+                                     complex64 with fp32 accumulation; LU,
+                                     Schur updates and apply stay complex128 */
+
+typedef struct fmmlu_tree fmmlu_tree;
+typedef struct fmmlu_handle fmmlu_handle;
+
+/* Options. Fill with fmmlu_default_opts and change fields as needed. */
+typedef struct fmmlu_opts {
+  int leaf_size;              /* s of Sec. 4: split a box while it holds more
+                                 than s points. Default 64. 1..4096          */
+  double eta;                 /* coupling of -i eta S; NaN means eta = k     */
+  double proxy_radius_factor; /* proxy sphere radius / box half-diagonal.
+                                 Default 1.5; must lie in (1, 2.88) so the
+                                 sphere encloses B and stays closer than
+                                 2.5 h, inside which P never reaches       */
+  int n_proxy;                /* proxy points per sphere (Fibonacci). 300   */
+  int precision;              /* FMMLU_PRECISION_*                           */
+  double eps_id_divisor;      /* ID tolerance eps_ID = eps / divisor. 1.0    */
+  int verbose;                /* 0 quiet, 1 per-level lines on stderr        */
+} fmmlu_opts;
+
+/* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if
+ * opts is NULL. */
+int fmmlu_default_opts(fmmlu_opts* opts);
+
+/* Build the level-restricted adaptive octree of Sec. 4 (preamble) and the
+ * per-level near/far lists and colour classes of Sec. 4.2-4.3.
+ *   points : device, N x 3 row-major doubles (caller order), read only
+ *   n      : number of points, >= 1
+ *   opts   : host, may be NULL (defaults)
+ *   out    : host, receives a new tree handle (free with fmmlu_free)
+ * Morton keys and the key sort run on the GPU; the box hierarchy, level
+ * restriction (2:1 balance over face/edge/corner contacts), neighbour lists
+ * and greedy colouring are built on the host from the sorted keys.
+ * Errors: INVALID_ARG (null, n < 1, non-finite point), OOM, CUDA. */
+int fmmlu_build_tree(const double* points, int64_t n, const fmmlu_opts* opts,
+                     void* stream, fmmlu_tree** out);
+
+/* Factor A (Sec. 4.2, RS-S with the proxy compression of Sec. 5.1).
+ *   tree    : from fmmlu_build_tree on the same points
+ *   points  : device, N x 3 (same array content as for the tree)
+ *   normals : device, N x 3 unit outward normals
+ *   weights : device, N positive quadrature weights
+ *   k       : wavenumber (> 0); eta from opts (NaN -> k)
+ *   eps     : ID tolerance in (0, 1): rank s = #{j : |R_jj| > eps |R_11|}
+ *   out     : receives the factorization handle; all factors stay resident
+ *             in device memory until fmmlu_free(handle)
+ * The tree may be freed after this call. Errors: INVALID_ARG, OOM, CUDA,
+ * SINGULAR_PIVOT, NONFINITE. */
+int fmmlu_factor(const fmmlu_tree* tree, const double* points,
+                 const double* normals, const double* weights, double k,
+                 double eps, const fmmlu_opts* opts, void* stream,
+                 fmmlu_handle** out);
+
+/* x = A^{-1} b with the stored factors (Sec. 4.2, factored form of A^{-1}):
+ * forward sweep in elimination order (E, L, D^{-1} per box), dense root
+ * solve, backward sweep in reverse order (U, F per box).
+ *   b, x : device, complex128, N x nrhs column-major (ld = N), caller order.
+ *          b and x may be the same array. b is not modified otherwise.
+ *   nrhs : >= 1
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int fmmlu_solve(const fmmlu_handle* h, const double* b, double* x, int nrhs,
+                void* stream);
+
+/* x = A^{-H} b with the same factors (conjugate-transposed sweeps: the
+ * forward sweep applies (F U)^H per box in elimination order, then the root
+ * A_tt^{-H}, then the backward sweep (L E)^H per box in reverse order).
+ * Same arguments and errors as fmmlu_solve. */
+int fmmlu_solve_adjoint(const fmmlu_handle* h, const double* b, double* x,
+                        int nrhs, void* stream);
+
+/* y = A v with A assembled on the fly from the kernel (no factorization; an
+ * independent dense product used for residuals). O(N^2) work.
+ *   tree : the tree of these points (used only for N); points, normals,
+ *          weights as for fmmlu_factor (device); v, y device complex128
+ *          N x nrhs column-major, caller order; y must not alias v.
+ * Errors: INVALID_ARG, CUDA. */
+int fmmlu_matvec(int64_t n, const double* points, const double* normals,
+                 const double* weights, double k, double eta, const double* v,
+                 double* y, int nrhs, void* stream);
+
+/* Write a JSON object with the factorization statistics into `json` (host,
+ * capacity `cap` bytes, always NUL-terminated when cap > 0): N, levels, n0,
+ * factor bytes (m_f), per-level box counts, colours, rank sums, timings.
+ * Returns the full length needed (excluding NUL), or a negative error code. */
+int fmmlu_stats(const fmmlu_handle* h, char* json, size_t cap);
+
+/* Write the tree as a flat int64 description into `out` (host, capacity
+ * `cap` int64 values) for inspection: header {n, nboxes, nlevels}, then per
+ * box {level, cx, cy, cz, start, end, parent, nchild}, then the Morton
+ * permutation (N values), then per level >= 2 and per level box
+ * {colour, n_near, near..., n_q, q...}. Returns the number of values needed,
+ * or a negative error code. */
+int64_t fmmlu_tree_describe(const fmmlu_tree* t, int64_t* out, int64_t cap);
+
+/* Free a tree or a factorization handle (either kind; NULL is a no-op). */
+void fmmlu_free(void* tree_or_handle);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* fmmlu_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMMLU_H */

@@ -1,0 +1,783 @@
+// C ABI and host scheduler of the FMM-LU factorization.
+//
+// Factorization (Sec. 4.2, RS-S): levels from the finest up to level 2. At
+// the start of a level the current boxes (level boxes plus coarser leaves)
+// get their level-start active lists (a parent's = the concatenation of its
+// children's skeletons), the Schur-update blocks of the previous level are
+// gathered into blocks between the new current boxes (k_merge), and the
+// per-box descriptors are uploaded. Boxes are then processed colour by
+// colour; each colour is one launch per step (gather rows, assemble the ID
+// matrix, CPQR + T, assemble the elimination blocks, the two X GEMMs, X_RR
+// inverse, W GEMM and the scattered Schur update). After the level the host
+// reads back the ranks and builds the next level. The stop rule of Sec. 4.2
+// (no box with active far DOFs) and the root block elimination follow.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <sstream>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fmmlu.h"
+#include "fmmlu_internal.h"
+#include "tree_host.h"
+
+using namespace fmmlu;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess)                                                                 \
+      throw Error(e_ == cudaErrorMemoryAllocation ? FMMLU_ERR_OOM : FMMLU_ERR_CUDA,        \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+constexpr uint32_t kTreeMagic = 0x54554d46u;    // "FMUT"
+constexpr uint32_t kHandleMagic = 0x48554d46u;  // "FMUH"
+
+template <typename T>
+T* dalloc(size_t count) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, count * sizeof(T)));
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+T* dupload(const std::vector<T>& v, cudaStream_t st) {
+  T* p = dalloc<T>(v.size());
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return p;
+}
+
+template <typename T>
+std::vector<T> ddownload(const T* p, size_t count, cudaStream_t st) {
+  std::vector<T> v(count);
+  if (count) CK(cudaMemcpyAsync(v.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return v;
+}
+
+// owns device allocations, freed in reverse order
+struct DevPool {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* get(size_t count) {
+    T* p = dalloc<T>(count);
+    ptrs.push_back(p);
+    return p;
+  }
+  template <typename T>
+  T* up(const std::vector<T>& v, cudaStream_t st) {
+    T* p = dupload(v, st);
+    ptrs.push_back(p);
+    return p;
+  }
+  void release() {
+    for (auto it = ptrs.rbegin(); it != ptrs.rend(); ++it) cudaFree(*it);
+    ptrs.clear();
+  }
+  ~DevPool() { release(); }
+};
+
+inline uint64_t pkey(int x, int y) { return ((uint64_t)(uint32_t)x << 32) | (uint32_t)y; }
+
+void default_opts(fmmlu_opts* o) {
+  o->leaf_size = 64;
+  o->eta = NAN;
+  o->proxy_radius_factor = 1.5;
+  o->n_proxy = 300;
+  o->precision = FMMLU_PRECISION_AUTO;
+  o->eps_id_divisor = 1.0;
+  o->verbose = 0;
+}
+
+fmmlu_opts checked_opts(const fmmlu_opts* in) {
+  fmmlu_opts o;
+  default_opts(&o);
+  if (in) o = *in;
+  if (o.leaf_size < 1 || o.leaf_size > 4096) throw Error(FMMLU_ERR_INVALID_ARG, "leaf_size out of [1, 4096]");
+  if (!(o.proxy_radius_factor > 1.0 && o.proxy_radius_factor < 2.88))
+    throw Error(FMMLU_ERR_INVALID_ARG, "proxy_radius_factor must lie in (1, 2.88)");
+  if (o.n_proxy < 8 || o.n_proxy > 100000) throw Error(FMMLU_ERR_INVALID_ARG, "n_proxy out of [8, 100000]");
+  if (o.precision < 0 || o.precision > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad precision");
+  if (!(o.eps_id_divisor > 0.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps_id_divisor must be > 0");
+  return o;
+}
+
+}  // namespace
+
+struct fmmlu_tree {
+  uint32_t magic = kTreeMagic;
+  TreeHost T;
+  int* d_perm = nullptr;
+  fmmlu_opts opts;
+  ~fmmlu_tree() { if (d_perm) cudaFree(d_perm); }
+};
+
+struct SolveSeg {
+  int b0, nb, rmax;
+};
+
+struct fmmlu_handle {
+  uint32_t magic = kHandleMagic;
+  int64_t n = 0;
+  double k = 0, eta = 0, eps = 0;
+  bool fp32 = false;
+  DevPool mem;                 // factors, plans, permutation
+  int* d_perm = nullptr;
+  SolveBox* d_boxes = nullptr;
+  std::vector<SolveSeg> segs;  // elimination order
+  int n0 = 0, nb_root = 64;
+  int* d_root_dofs = nullptr;
+  double2* d_root = nullptr;
+  std::string stats;
+  int64_t factor_entries = 0;  // complex entries of the stored factors (m_f / 16)
+  int64_t arena_bytes = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// level state
+// ---------------------------------------------------------------------------
+
+struct LevelState {
+  int level = 0;
+  std::vector<int> cur;                    // tree ids of current boxes
+  std::unordered_map<int, int> cidx;       // tree id -> current index
+  std::vector<int> a0, off;                // per current box
+  std::vector<int> act_dof;                // level-start DOFs (concatenated)
+  std::vector<int> cur_n, act_pos;         // after processing (host copies)
+  std::unordered_map<uint64_t, int64_t> pair;   // (cur x, cur y) -> pool offset
+  std::vector<std::pair<int, int>> pair_list;
+  DevPool mem;
+  int *d_cur_n = nullptr, *d_cur_off = nullptr, *d_cur_a0 = nullptr;
+  int *d_act_dof = nullptr, *d_act_pos = nullptr;
+  double2* d_pool = nullptr;
+  int64_t pool_size = 0;
+  int64_t total() const { return (int64_t)act_dof.size(); }
+  // current active DOFs of current box c (after processing)
+  void active_dofs(int c, std::vector<int>& out) const {
+    for (int i = 0; i < cur_n[c]; ++i) out.push_back(act_dof[off[c] + act_pos[off[c] + i]]);
+  }
+};
+
+std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const LevelState* prev,
+                                       const HLevel* lists, cudaStream_t st) {
+  auto L = std::make_unique<LevelState>();
+  L->level = level;
+  L->cur = current_boxes(T, level);
+  int nc = (int)L->cur.size();
+  for (int c = 0; c < nc; ++c) L->cidx[L->cur[c]] = c;
+  L->a0.resize(nc);
+  L->off.resize(nc);
+  for (int c = 0; c < nc; ++c) {
+    int X = L->cur[c];
+    const HBox& b = T.boxes[X];
+    L->off[c] = (int)L->act_dof.size();
+    if (b.level == level && !b.leaf()) {
+      for (int ch : b.kids) {
+        auto it = prev->cidx.find(ch);
+        if (it == prev->cidx.end()) throw Error(FMMLU_ERR_CUDA, "internal: child not current");
+        prev->active_dofs(it->second, L->act_dof);
+      }
+    } else {
+      for (int64_t p = b.start; p < b.end; ++p) L->act_dof.push_back((int)p);
+    }
+    L->a0[c] = (int)L->act_dof.size() - L->off[c];
+  }
+  L->cur_n = L->a0;
+  L->act_pos.resize(L->act_dof.size());
+  for (int c = 0; c < nc; ++c)
+    for (int i = 0; i < L->a0[c]; ++i) L->act_pos[L->off[c] + i] = i;
+  // pair set: images of the previous pairs, plus closed-neighbourhood pairs
+  auto add = [&](int x, int y) {
+    uint64_t key = pkey(x, y);
+    if (L->pair.count(key)) return;
+    L->pair[key] = -1;
+    L->pair_list.push_back({x, y});
+  };
+  auto image = [&](int prev_c) -> int {
+    int X = prev->cur[prev_c];
+    const HBox& b = T.boxes[X];
+    int Y = b.level == level + 1 ? b.parent : X;
+    return L->cidx.at(Y);
+  };
+  if (prev)
+    for (auto& pr : prev->pair_list) add(image(pr.first), image(pr.second));
+  if (lists) {
+    for (size_t r = 0; r < lists->boxes.size(); ++r) {
+      std::vector<int> cn = {L->cidx.at(lists->boxes[r])};
+      for (int j = lists->nbeg[r]; j < lists->nbeg[r] + lists->ncnt[r]; ++j)
+        cn.push_back(L->cidx.at(lists->nlist[j]));
+      for (int x : cn)
+        for (int y : cn) add(x, y);
+    }
+  }
+  int64_t tot = 0;
+  for (auto& pr : L->pair_list) {
+    L->pair[pkey(pr.first, pr.second)] = tot;
+    tot += (int64_t)L->a0[pr.first] * L->a0[pr.second];
+  }
+  L->pool_size = tot;
+  L->d_pool = L->mem.get<double2>((size_t)tot);
+  if (tot) CK(cudaMemsetAsync(L->d_pool, 0, (size_t)tot * sizeof(double2), st));
+  L->d_cur_n = L->mem.up(L->cur_n, st);
+  L->d_cur_off = L->mem.up(L->off, st);
+  L->d_cur_a0 = L->mem.up(L->a0, st);
+  L->d_act_dof = L->mem.up(L->act_dof, st);
+  L->d_act_pos = L->mem.up(L->act_pos, st);
+  // gather the previous Schur blocks into the new pool
+  if (prev && !prev->pair_list.empty()) {
+    std::vector<MergeItem> items;
+    std::vector<int> suboff(prev->cur.size(), 0);   // offset of prev box inside its image
+    {
+      std::unordered_map<int, int> run;   // image -> running offset (children in order)
+      for (size_t c = 0; c < prev->cur.size(); ++c) {
+        int X = prev->cur[c];
+        const HBox& b = T.boxes[X];
+        if (b.level == level + 1) {
+          // children of one parent are consecutive in current order (by start)
+          int img = L->cidx.at(b.parent);
+          int& o = run[img];
+          suboff[c] = o;
+          o += prev->cur_n[c];
+        }
+      }
+    }
+    for (auto& pr : prev->pair_list) {
+      int x = pr.first, y = pr.second;
+      int X = image(x), Y = image(y);
+      MergeItem it;
+      it.src = prev->d_pool + prev->pair.at(pkey(x, y));
+      it.dst = L->d_pool + L->pair.at(pkey(X, Y));
+      it.ld_src = prev->a0[x];
+      it.ld_dst = L->a0[X];
+      it.off_i = suboff[x];
+      it.off_j = suboff[y];
+      it.ni = prev->cur_n[x];
+      it.nj = prev->cur_n[y];
+      it.pos_i = prev->d_act_pos + prev->off[x];
+      it.pos_j = prev->d_act_pos + prev->off[y];
+      if (it.ni > 0 && it.nj > 0) items.push_back(it);
+    }
+    MergeItem* d_items = L->mem.up(items, st);
+    launch_merge(d_items, (int)items.size(), 0, 0, st);
+    CK(cudaGetLastError());
+  }
+  return L;
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+int status_to_code(int s, std::string& msg) {
+  if (s & kStatusSingular) { msg = "singular pivot in X_RR or a root block"; return FMMLU_ERR_SINGULAR_PIVOT; }
+  if (s & kStatusNonfinite) { msg = "non-finite value in an ID matrix"; return FMMLU_ERR_NONFINITE; }
+  if (s & kStatusBound) { msg = "internal size bound exceeded"; return FMMLU_ERR_LIMIT; }
+  return 0;
+}
+
+void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, const double* w,
+                 double k, double eps, const fmmlu_opts& opt, cudaStream_t st, fmmlu_handle* H) {
+  const TreeHost& T = tree->T;
+  const int64_t n = T.n;
+  H->n = n;
+  H->k = k;
+  H->eta = std::isnan(opt.eta) ? k : opt.eta;
+  H->eps = eps;
+  H->fp32 = opt.precision == FMMLU_PRECISION_MIXED ||
+            (opt.precision == FMMLU_PRECISION_AUTO && eps >= 1e-5);
+  const double eps_id = eps / opt.eps_id_divisor;
+  Timer total_timer;
+  DevPool work;   // freed at the end of the factorization
+  H->d_perm = H->mem.get<int>((size_t)n);
+  CK(cudaMemcpyAsync(H->d_perm, tree->d_perm, n * sizeof(int), cudaMemcpyDeviceToDevice, st));
+  double* soa = work.get<double>((size_t)n * 8);
+  launch_permute_geometry(pts, nrm, w, tree->d_perm, n, soa, st);
+  CK(cudaGetLastError());
+  Geometry g{soa, soa + n, soa + 2 * n, soa + 3 * n, soa + 4 * n, soa + 5 * n, soa + 6 * n,
+             soa + 7 * n, k, H->eta};
+  int* d_status = work.get<int>(1);
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+
+  std::ostringstream js;
+  js << "{\"n\": " << n << ", \"k\": " << k << ", \"eta\": " << H->eta << ", \"eps\": " << eps
+     << ", \"precision\": \"" << (H->fp32 ? "mixed" : "fp64") << "\", \"nlevels\": " << T.nlevels
+     << ", \"levels\": [";
+  std::vector<SolveBox> plan;
+  std::unique_ptr<LevelState> prev;
+  int root_level = 1;
+  bool first_level = true;
+  for (int lev = T.nlevels - 1; lev >= 2; --lev) {
+    Timer lt;
+    const HLevel& HL = T.levels.at(lev);
+    auto L = make_level(T, lev, prev.get(), &HL, st);
+    CK(cudaStreamSynchronize(st));   // the merge has read the previous level
+    prev.reset();
+    // stop rule: any level box with active far DOFs?
+    const int nb = (int)HL.boxes.size();
+    bool far_any = false;
+    for (int r = 0; r < nb && !far_any; ++r) {
+      int64_t closed = L->a0[L->cidx.at(HL.boxes[r])];
+      for (int j = HL.nbeg[r]; j < HL.nbeg[r] + HL.ncnt[r]; ++j) closed += L->a0[L->cidx.at(HL.nlist[j])];
+      if (L->total() - closed > 0) far_any = true;
+    }
+    if (!far_any) {
+      root_level = lev;
+      prev = std::move(L);
+      break;
+    }
+    // descriptors in elimination order
+    std::vector<BoxDesc> desc(nb);
+    std::vector<int> nlist, qlist;
+    std::vector<int64_t> pairtab, qpair;
+    std::vector<int> seg_start;
+    int64_t arena = 0, iarena = 0;
+    const double hreal = T.side / (double)(1 << lev);
+    for (int e = 0; e < nb; ++e) {
+      int r = HL.order[e];
+      int B = HL.boxes[r];
+      const HBox& hb = T.boxes[B];
+      BoxDesc& d = desc[e];
+      std::memset(&d, 0, sizeof(d));
+      d.cur = L->cidx.at(B);
+      d.a = L->a0[d.cur];
+      d.nbeg = (int)nlist.size();
+      d.ncnt = HL.ncnt[r];
+      d.nmax = 0;
+      for (int j = HL.nbeg[r]; j < HL.nbeg[r] + HL.ncnt[r]; ++j) {
+        int c = L->cidx.at(HL.nlist[j]);
+        nlist.push_back(c);
+        d.nmax += L->a0[c];
+      }
+      d.qbeg = (int)qlist.size();
+      d.qcnt = HL.qcnt[r];
+      d.qmax = 0;
+      for (int j = HL.qbeg[r]; j < HL.qbeg[r] + HL.qcnt[r]; ++j) {
+        int c = L->cidx.at(HL.qlist[j]);
+        qlist.push_back(c);
+        d.qmax += L->a0[c];
+      }
+      d.mmax = 2 * d.qmax + 2 * opt.n_proxy;
+      d.h = hreal;
+      d.cx = T.corner[0] + ((double)hb.cx + 0.5) * hreal;
+      d.cy = T.corner[1] + ((double)hb.cy + 0.5) * hreal;
+      d.cz = T.corner[2] + ((double)hb.cz + 0.5) * hreal;
+      std::vector<int> cn = {d.cur};
+      for (int j = 0; j < d.ncnt; ++j) cn.push_back(nlist[d.nbeg + j]);
+      d.pairtab = (int64_t)pairtab.size();
+      for (int x : cn)
+        for (int y : cn) {
+          auto it = L->pair.find(pkey(x, y));
+          pairtab.push_back(it == L->pair.end() ? -1 : it->second);
+        }
+      d.qpair = (int64_t)qpair.size();
+      for (int j = 0; j < d.qcnt; ++j) {
+        int c = qlist[d.qbeg + j];
+        auto i1 = L->pair.find(pkey(c, d.cur));
+        auto i2 = L->pair.find(pkey(d.cur, c));
+        qpair.push_back(i1 == L->pair.end() ? -1 : i1->second);
+        qpair.push_back(i2 == L->pair.end() ? -1 : i2->second);
+      }
+      int64_t a = d.a, nm = d.nmax;
+      d.G1_off = arena; arena += a * (a + nm);
+      d.G3_off = arena; arena += (a + nm) * a;
+      d.T_off = arena; arena += a * a;
+      d.Xinv_off = arena; arena += a * a;
+      d.idx_off = iarena; iarena += (a + nm) + a;
+      if (e == 0 || HL.colour[HL.order[e - 1]] != HL.colour[r]) seg_start.push_back(e);
+    }
+    seg_start.push_back(nb);
+    // per-colour scratch offsets (reset at each colour start)
+    int64_t rows_max = 0, M_max = 0, W_max = 0;
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+      int64_t ro = 0, mo = 0, wo = 0;
+      for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
+        BoxDesc& d = desc[e];
+        d.rows_off = ro; ro += 3 * (int64_t)(d.qmax + d.nmax);
+        d.M_off = mo; mo += (int64_t)d.mmax * d.a;
+        d.W_off = wo; wo += (int64_t)(d.a + d.nmax) * d.a;
+      }
+      rows_max = std::max(rows_max, ro);
+      M_max = std::max(M_max, mo);
+      W_max = std::max(W_max, wo);
+    }
+    DevPool lw;   // level scratch
+    double2* d_arena = H->mem.get<double2>((size_t)arena);
+    int* d_iarena = H->mem.get<int>((size_t)iarena);
+    H->arena_bytes += arena * 16 + iarena * 4;
+    LevelDev LD;
+    LD.desc = lw.up(desc, st);
+    BoxRun* d_run = lw.get<BoxRun>((size_t)nb);
+    CK(cudaMemsetAsync(d_run, 0, nb * sizeof(BoxRun), st));
+    LD.run = d_run;
+    LD.nlist = lw.up(nlist, st);
+    LD.qlist = lw.up(qlist, st);
+    LD.pairtab = lw.up(pairtab, st);
+    LD.qpair = lw.up(qpair, st);
+    LD.cur_n = L->d_cur_n;
+    LD.cur_off = L->d_cur_off;
+    LD.cur_a0 = L->d_cur_a0;
+    LD.act_dof = L->d_act_dof;
+    LD.act_pos = L->d_act_pos;
+    LD.delta = L->d_pool;
+    LD.rows = lw.get<int>((size_t)rows_max);
+    LD.Mbuf = H->fp32 ? (void*)lw.get<float2>((size_t)M_max) : (void*)lw.get<double2>((size_t)M_max);
+    LD.Wbuf = lw.get<double2>((size_t)W_max);
+    LD.arena = d_arena;
+    LD.iarena = d_iarena;
+    LD.n_proxy = opt.n_proxy;
+    LD.proxy_factor = opt.proxy_radius_factor;
+    LD.eps = eps_id;
+    LD.status = d_status;
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+      int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
+      int amax = 1, mmax = 1, nmaxm = 0;
+      for (int e = b0; e < b0 + cnt; ++e) {
+        amax = std::max(amax, desc[e].a);
+        mmax = std::max(mmax, desc[e].mmax);
+        nmaxm = std::max(nmaxm, desc[e].nmax);
+      }
+      launch_gather_rows(LD, b0, cnt, st);
+      launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
+      launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
+      launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
+      launch_elim_gemms(LD, b0, cnt, amax, nmaxm, st);
+      launch_xrr_inverse(LD, b0, cnt, amax, st);
+      launch_schur(LD, b0, cnt, amax, nmaxm, st);
+      CK(cudaGetLastError());
+    }
+    std::vector<BoxRun> run = ddownload(d_run, (size_t)nb, st);
+    int status = ddownload(d_status, 1, st)[0];
+    std::string msg;
+    if (int code = status_to_code(status, msg)) throw Error(code, msg + " (level " + std::to_string(lev) + ")");
+    L->cur_n = ddownload(L->d_cur_n, L->cur.size(), st);
+    L->act_pos = ddownload(L->d_act_pos, L->act_pos.size(), st);
+    // solve plan for this level
+    int64_t sum_a = 0, sum_s = 0, max_a = 0, max_r = 0;
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+      int b0p = (int)plan.size();
+      int rmax = 0;
+      for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
+        const BoxDesc& d = desc[e];
+        const BoxRun& rr = run[e];
+        sum_a += d.a; sum_s += rr.s;
+        max_a = std::max<int64_t>(max_a, d.a);
+        max_r = std::max<int64_t>(max_r, rr.r);
+        if (rr.r == 0) continue;
+        int64_t ld3 = d.a + d.nmax;
+        SolveBox sb;
+        sb.r = rr.r; sb.s = rr.s; sb.n = rr.n; sb.pad_ = 0;
+        sb.idx = d_iarena + d.idx_off;
+        sb.T = d_arena + d.T_off; sb.ldT = d.a;
+        sb.Xinv = d_arena + d.Xinv_off; sb.ldX = d.a;
+        sb.XCR = d_arena + d.G3_off + (int64_t)rr.s * ld3; sb.ldL = (int)ld3;
+        sb.XRC = d_arena + d.G1_off + rr.s; sb.ldU = d.a;
+        plan.push_back(sb);
+        rmax = std::max(rmax, rr.r);
+        H->factor_entries += (int64_t)rr.s * rr.r + (int64_t)rr.r * rr.r +
+                             2 * (int64_t)(rr.s + rr.n) * rr.r;
+      }
+      int cnt = (int)plan.size() - b0p;
+      if (cnt > 0) H->segs.push_back({b0p, cnt, rmax});
+    }
+    double lms = lt.ms();
+    if (opt.verbose)
+      std::fprintf(stderr, "[fmmlu] level %d: boxes %d colours %d current %zu sum_a %lld sum_s %lld max_a %lld max_r %lld pool %.1f MB %.1f ms\n",
+                   lev, nb, HL.ncolours, L->cur.size(), (long long)sum_a, (long long)sum_s,
+                   (long long)max_a, (long long)max_r, L->pool_size * 16.0 / 1e6, lms);
+    js << (first_level ? "" : ", ") << "{\"level\": " << lev << ", \"boxes\": " << nb
+       << ", \"colours\": " << HL.ncolours << ", \"current\": " << L->cur.size()
+       << ", \"sum_a\": " << sum_a << ", \"sum_s\": " << sum_s << ", \"max_a\": " << max_a
+       << ", \"max_r\": " << max_r << ", \"ms\": " << lms << "}";
+    first_level = false;
+    prev = std::move(L);
+  }
+  // ---- root ----------------------------------------------------------------
+  Timer rt;
+  std::unique_ptr<LevelState> R;
+  if (prev && prev->level == root_level) {
+    R = std::move(prev);
+  } else {
+    R = make_level(T, root_level, prev.get(), nullptr, st);
+    CK(cudaStreamSynchronize(st));
+    prev.reset();
+  }
+  int n0 = (int)R->total();
+  H->n0 = n0;
+  if (n0 > 0) {
+    int nc = (int)R->cur.size();
+    std::vector<int> owner(n0), pos(n0);
+    for (int c = 0; c < nc; ++c)
+      for (int i = 0; i < R->a0[c]; ++i) { owner[R->off[c] + i] = c; pos[R->off[c] + i] = i; }
+    std::vector<int64_t> pairoff((size_t)nc * nc, -1);
+    for (auto& kv : R->pair) pairoff[(size_t)(kv.first >> 32) * nc + (uint32_t)kv.first] = kv.second;
+    DevPool rw;
+    int* d_owner = rw.up(owner, st);
+    int* d_pos = rw.up(pos, st);
+    int64_t* d_pairoff = rw.up(pairoff, st);
+    H->d_root_dofs = H->mem.up(R->act_dof, st);
+    H->d_root = H->mem.get<double2>((size_t)n0 * n0);
+    launch_assemble_root(g, H->d_root_dofs, d_owner, d_pos, d_pairoff, R->d_cur_a0, nc, R->d_pool,
+                         n0, H->d_root, st);
+    double2* wk = rw.get<double2>((size_t)n0 * H->nb_root);
+    launch_root_factor(H->d_root, n0, H->nb_root, wk, d_status, st);
+    CK(cudaGetLastError());
+    int status = ddownload(d_status, 1, st)[0];
+    std::string msg;
+    if (int code = status_to_code(status, msg)) throw Error(code, msg + " (root)");
+    H->factor_entries += (int64_t)n0 * n0;
+  }
+  double root_ms = rt.ms();
+  H->d_boxes = H->mem.up(plan, st);
+  CK(cudaStreamSynchronize(st));
+  double tot_ms = total_timer.ms();
+  if (opt.verbose)
+    std::fprintf(stderr, "[fmmlu] root level %d n0 %d %.1f ms; factor %.1f ms; m_f %.1f MB\n",
+                 root_level, n0, root_ms, tot_ms, H->factor_entries * 16.0 / 1e6);
+  js << "], \"root_level\": " << root_level << ", \"n0\": " << n0 << ", \"root_ms\": " << root_ms
+     << ", \"factor_ms\": " << tot_ms << ", \"factor_bytes\": " << H->factor_entries * 16
+     << ", \"arena_bytes\": " << H->arena_bytes << ", \"eliminated_boxes\": " << plan.size()
+     << ", \"colour_segments\": " << H->segs.size() << "}";
+  H->stats = js.str();
+}
+
+void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, bool adjoint,
+                cudaStream_t st) {
+  int64_t n = H->n;
+  DevPool w;
+  double2* v = w.get<double2>((size_t)n * nrhs);
+  launch_gather_vec(reinterpret_cast<const double2*>(b), H->d_perm, n, nrhs, v, st);
+  for (const auto& sg : H->segs)
+    launch_sweep(H->d_boxes, sg.b0, sg.nb, sg.rmax, v, n, nrhs, false, adjoint, st);
+  if (H->n0 > 0) {
+    int n0 = H->n0;
+    double2* vr = w.get<double2>((size_t)n0 * nrhs);
+    double2* z = w.get<double2>((size_t)n0 * nrhs);
+    int nblk = std::max(1, (n0 + 511) / 512);
+    double2* partial = w.get<double2>((size_t)nrhs * nblk * 256);
+    launch_root_gather(v, H->d_root_dofs, n0, n, nrhs, vr, st);
+    launch_root_solve(H->d_root, n0, H->nb_root, vr, z, partial, nrhs, adjoint, st);
+    launch_root_scatter(vr, H->d_root_dofs, n0, n, nrhs, v, st);
+  }
+  for (auto it = H->segs.rbegin(); it != H->segs.rend(); ++it)
+    launch_sweep(H->d_boxes, it->b0, it->nb, it->rmax, v, n, nrhs, true, adjoint, st);
+  launch_scatter_vec(v, H->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));   // the work buffers are freed on return
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// exported C ABI
+// ---------------------------------------------------------------------------
+
+namespace {
+int guard(const std::function<void()>& f) {
+  try {
+    f();
+    g_err.clear();
+    return FMMLU_OK;
+  } catch (const Error& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return FMMLU_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return FMMLU_ERR_CUDA;
+  } catch (...) {
+    g_err = "unknown error";
+    return FMMLU_ERR_CUDA;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int fmmlu_default_opts(fmmlu_opts* opts) {
+  if (!opts) { g_err = "opts is NULL"; return FMMLU_ERR_INVALID_ARG; }
+  default_opts(opts);
+  return FMMLU_OK;
+}
+
+const char* fmmlu_last_error(void) { return g_err.c_str(); }
+
+int fmmlu_build_tree(const double* points, int64_t n, const fmmlu_opts* opts, void* stream,
+                     fmmlu_tree** out) {
+  return guard([&] {
+    if (!points || !out || n < 1) throw Error(FMMLU_ERR_INVALID_ARG, "null argument or n < 1");
+    if (n > (int64_t)1 << 30) throw Error(FMMLU_ERR_LIMIT, "n above 2^30");
+    *out = nullptr;
+    fmmlu_opts o = checked_opts(opts);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> p((size_t)n * 3);
+    CK(cudaMemcpyAsync(p.data(), points, p.size() * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+    for (int64_t i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) {
+        double v = p[3 * i + a];
+        if (!std::isfinite(v)) throw Error(FMMLU_ERR_INVALID_ARG, "non-finite point coordinate");
+        lo[a] = std::min(lo[a], v);
+        hi[a] = std::max(hi[a], v);
+      }
+    auto t = std::make_unique<fmmlu_tree>();
+    t->opts = o;
+    TreeHost& T = t->T;
+    T.n = n;
+    double extent = 0;
+    double center[3];
+    for (int a = 0; a < 3; ++a) {
+      center[a] = (lo[a] + hi[a]) / 2.0;
+      extent = std::max(extent, hi[a] - lo[a]);
+    }
+    double side = extent * (1.0 + 1e-12);
+    if (!(side > 0.0)) side = 1.0;
+    T.side = side;
+    for (int a = 0; a < 3; ++a) T.corner[a] = center[a] - side / 2.0;
+    T.keys.resize(n);
+    T.perm.resize(n);
+    int rc = gpu_morton_sort(points, n, T.corner, side, T.keys.data(), T.perm.data(), st);
+    if (rc) throw Error(FMMLU_ERR_CUDA, std::string("morton sort: ") + cudaGetErrorString((cudaError_t)rc));
+    build_host_tree(T, o.leaf_size);
+    t->d_perm = dupload(T.perm, st);
+    CK(cudaStreamSynchronize(st));
+    *out = t.release();
+  });
+}
+
+int fmmlu_factor(const fmmlu_tree* tree, const double* points, const double* normals,
+                 const double* weights, double k, double eps, const fmmlu_opts* opts,
+                 void* stream, fmmlu_handle** out) {
+  return guard([&] {
+    if (!tree || tree->magic != kTreeMagic || !points || !normals || !weights || !out)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument or not a tree");
+    if (!(k > 0.0) || !std::isfinite(k)) throw Error(FMMLU_ERR_INVALID_ARG, "k must be positive");
+    if (!(eps > 0.0 && eps < 1.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps must lie in (0, 1)");
+    *out = nullptr;
+    fmmlu_opts o = checked_opts(opts ? opts : &tree->opts);
+    auto H = std::make_unique<fmmlu_handle>();
+    factor_impl(tree, points, normals, weights, k, eps, o, (cudaStream_t)stream, H.get());
+    *out = H.release();
+  });
+}
+
+int fmmlu_solve(const fmmlu_handle* h, const double* b, double* x, int nrhs, void* stream) {
+  return guard([&] {
+    if (!h || h->magic != kHandleMagic || !b || !x || nrhs < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
+    solve_impl(h, b, x, nrhs, false, (cudaStream_t)stream);
+  });
+}
+
+int fmmlu_solve_adjoint(const fmmlu_handle* h, const double* b, double* x, int nrhs,
+                        void* stream) {
+  return guard([&] {
+    if (!h || h->magic != kHandleMagic || !b || !x || nrhs < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
+    solve_impl(h, b, x, nrhs, true, (cudaStream_t)stream);
+  });
+}
+
+int fmmlu_matvec(int64_t n, const double* points, const double* normals, const double* weights,
+                 double k, double eta, const double* v, double* y, int nrhs, void* stream) {
+  return guard([&] {
+    if (n < 1 || !points || !normals || !weights || !v || !y || nrhs < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, n < 1 or nrhs < 1");
+    if (v == y) throw Error(FMMLU_ERR_INVALID_ARG, "y must not alias v");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevPool w;
+    std::vector<int> iota((size_t)n);
+    std::iota(iota.begin(), iota.end(), 0);
+    int* d_id = w.up(iota, st);
+    double* soa = w.get<double>((size_t)n * 8);
+    launch_permute_geometry(points, normals, weights, d_id, n, soa, st);
+    Geometry g{soa, soa + n, soa + 2 * n, soa + 3 * n, soa + 4 * n, soa + 5 * n, soa + 6 * n,
+               soa + 7 * n, k, std::isnan(eta) ? k : eta};
+    launch_matvec(g, n, reinterpret_cast<const double2*>(v), reinterpret_cast<double2*>(y), nrhs,
+                  st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+  });
+}
+
+int fmmlu_stats(const fmmlu_handle* h, char* json, size_t cap) {
+  if (!h || h->magic != kHandleMagic) { g_err = "not a handle"; return FMMLU_ERR_INVALID_ARG; }
+  const std::string& s = h->stats;
+  if (json && cap > 0) {
+    size_t m = std::min(cap - 1, s.size());
+    std::memcpy(json, s.data(), m);
+    json[m] = 0;
+  }
+  return (int)s.size();
+}
+
+int64_t fmmlu_tree_describe(const fmmlu_tree* t, int64_t* out, int64_t cap) {
+  if (!t || t->magic != kTreeMagic) { g_err = "not a tree"; return FMMLU_ERR_INVALID_ARG; }
+  const TreeHost& T = t->T;
+  std::vector<int64_t> v;
+  v.push_back(T.n);
+  v.push_back((int64_t)T.boxes.size());
+  v.push_back(T.nlevels);
+  for (const HBox& b : T.boxes) {
+    v.push_back(b.level); v.push_back(b.cx); v.push_back(b.cy); v.push_back(b.cz);
+    v.push_back(b.start); v.push_back(b.end); v.push_back(b.parent);
+    v.push_back((int64_t)b.kids.size());
+  }
+  for (int p : T.perm) v.push_back(p);
+  for (int l = 2; l < T.nlevels; ++l) {
+    const HLevel& L = T.levels.at(l);
+    for (size_t r = 0; r < L.boxes.size(); ++r) {
+      v.push_back(L.colour[r]);
+      v.push_back(L.ncnt[r]);
+      for (int j = L.nbeg[r]; j < L.nbeg[r] + L.ncnt[r]; ++j) v.push_back(L.nlist[j]);
+      v.push_back(L.qcnt[r]);
+      for (int j = L.qbeg[r]; j < L.qbeg[r] + L.qcnt[r]; ++j) v.push_back(L.qlist[j]);
+    }
+  }
+  if (out) std::memcpy(out, v.data(), sizeof(int64_t) * (size_t)std::min<int64_t>(cap, (int64_t)v.size()));
+  return (int64_t)v.size();
+}
+
+void fmmlu_free(void* p) {
+  if (!p) return;
+  uint32_t m;
+  std::memcpy(&m, p, sizeof(m));
+  if (m == kTreeMagic) {
+    auto* t = static_cast<fmmlu_tree*>(p);
+    t->magic = 0;
+    delete t;
+  } else if (m == kHandleMagic) {
+    auto* h = static_cast<fmmlu_handle*>(p);
+    h->magic = 0;
+    delete h;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Device helpers: complex arithmetic and the Helmholtz kernel evaluations.
+//
+// Kernel definitions (Sec. 3):
+//   G(x, y) = exp(i k r) / (4 pi r),  r = |x - y|            (Eq. greenfunhelm)
+//   K(x, y) = n(y) . grad_y G(x, y) - i eta G(x, y)            (Eq. comb_ref)
+//   n(y) . grad_y G = G (i k r - 1) / r^2 ((y - x) . n(y))
+//   A_ij = sqrt(w_i) K(x_i, x_j) sqrt(w_j) (i != j),
+//   A_ii = 1/2 - i eta (sqrt(w_i/pi)/2 + i k w_i/(4 pi))       (Eq. disc3)
+// The transcendental functions are CUDA's own (sincos, sqrt, division).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "fmmlu_internal.h"
+
+namespace fmmlu {
+
+template <typename R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return mk(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return mk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfma_cj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return mk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return mk(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return mk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ void cfma_cj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  float d = b.x * b.x + b.y * b.y;
+  return mk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+template <typename C> __device__ __forceinline__ C from_d2(double2 a);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+// G(t, s) = exp(i k r)/(4 pi r)
+__device__ __forceinline__ double2 green(double tx, double ty, double tz, double sx,
+                                         double sy, double sz, double k) {
+  double dx = sx - tx, dy = sy - ty, dz = sz - tz;
+  double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double sn, cs;
+  sincos(k * r, &sn, &cs);
+  double g = 1.0 / (4.0 * kPi * r);
+  return mk(cs * g, sn * g);
+}
+
+// K(t, s) = n(s).grad_s G(t, s) - i eta G(t, s)
+__device__ __forceinline__ double2 comb_kernel(double tx, double ty, double tz,
+                                               double sx, double sy, double sz,
+                                               double nx, double ny, double nz,
+                                               double k, double eta) {
+  double dx = sx - tx, dy = sy - ty, dz = sz - tz;
+  double r2 = dx * dx + dy * dy + dz * dz;
+  double r = sqrt(r2);
+  double sn, cs;
+  sincos(k * r, &sn, &cs);
+  double ginv = 1.0 / (4.0 * kPi * r);
+  double2 g = mk(cs * ginv, sn * ginv);
+  double proj = (dx * nx + dy * ny + dz * nz) / r2;   // ((s - t).n(s)) / r^2
+  // (i k r - 1) * proj
+  double2 f = mk(-proj, k * r * proj);
+  double2 d = cmul(g, f);
+  // - i eta g = (eta g.y, -eta g.x)
+  return mk(d.x + eta * g.y, d.y - eta * g.x);
+}
+
+// Matrix entry A(i, j) of the scaled system without Schur updates.
+__device__ __forceinline__ double2 entry(const Geometry& g, int i, int j) {
+  if (i == j) {
+    double w = g.w[i];
+    return mk(0.5 + g.eta * g.k * w / (4.0 * kPi), -g.eta * sqrt(w / kPi) * 0.5);
+  }
+  double2 kv = comb_kernel(g.px[i], g.py[i], g.pz[i], g.px[j], g.py[j], g.pz[j],
+                           g.nx[j], g.ny[j], g.nz[j], g.k, g.eta);
+  return cscale(kv, g.sw[i] * g.sw[j]);
+}
+
+// l-th of n Fibonacci points on the unit sphere
+__device__ __forceinline__ void fib_point(int l, int n, double& ux, double& uy,
+                                          double& uz) {
+  double z = 1.0 - (2.0 * l + 1.0) / n;
+  double phi = l * kGoldenAngle;
+  double rho = sqrt(fmax(0.0, 1.0 - z * z));
+  double sn, cs;
+  sincos(phi, &sn, &cs);
+  ux = rho * cs; uy = rho * sn; uz = z;
+}
+
+__device__ __forceinline__ void set_status(int* status, int bits) {
+  if (status) atomicOr(status, bits);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace fmmlu

@@ -1,0 +1,151 @@
+// Internal declarations shared by the FMM-LU CUDA translation units.
+//
+// Layout conventions (device):
+//  * points are Morton-sorted; DOF i is the i-th sorted point. Coordinates are
+//    stored SoA: px, py, pz, nx, ny, nz, w, sqrt(w) (float64).
+//  * complex128 is double2 (x = re, y = im); complex64 is float2.
+//  * every dense block is column-major.
+//  * "current boxes" of a level: the boxes of that level plus all coarser
+//    leaves. Each has a level-start active list act0 (DOF ids) and a current
+//    active subset given by positions into act0 (act_pos, first cur_n used).
+//  * Schur updates are kept per ordered pair of current boxes (X, Y) as a dense
+//    a0(X) x a0(Y) block (leading dimension a0(X)) indexed by act0 positions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fmmlu {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kGoldenAngle = 2.39996322972865332223;  // pi (3 - sqrt 5)
+
+// device status bits (kernels never trap; they set bits and return)
+enum StatusBits : int {
+  kStatusSingular = 1,
+  kStatusNonfinite = 2,
+  kStatusBound = 4,      // an internal size bound was exceeded
+};
+
+struct Geometry {        // sorted SoA copies of the inputs
+  const double* px; const double* py; const double* pz;
+  const double* nx; const double* ny; const double* nz;
+  const double* w;  const double* sw;
+  double k, eta;
+};
+
+// one per box processed at a level (host-built)
+struct BoxDesc {
+  int cur;          // current-box index of B
+  int a;            // actives at level start
+  int nbeg, ncnt;   // N boxes: nlist[nbeg .. nbeg + ncnt) (current indices)
+  int qbeg, qcnt;   // Q boxes: qlist[...]
+  int nmax;         // sum of a0 over N boxes
+  int qmax;         // sum of a0 over Q boxes
+  int mmax;         // 2 qmax + 2 n_proxy
+  int pad_;
+  double cx, cy, cz, h;   // centre and side of B
+  int64_t pairtab;  // offset of the (1+ncnt)^2 table of Delta offsets over
+                    // cn = [B, N...] (row-major [x][y]), -1 = no block
+  int64_t qpair;    // offset of 2*qcnt Delta offsets: (Delta(C,B), Delta(B,C))
+  int64_t rows_off; // int scratch: qdof,qpos,qloc (3 qmax), ndof,npos,nloc (3 nmax)
+  int64_t M_off;    // ID matrix scratch (mmax x a), complex units of the ID type
+  int64_t W_off;    // Schur scratch ((a + nmax) x a), ld a + nmax
+  int64_t G1_off;   // factor arena: a x (a + nmax), ld a   rows [S|R], cols [S|N|R]
+  int64_t G3_off;   // factor arena: (a + nmax) x a, ld a + nmax  rows [S|N|R], cols [S|R]
+  int64_t T_off;    // factor arena: s x r, ld a
+  int64_t Xinv_off; // factor arena: r x r, ld a
+  int64_t idx_off;  // int arena: [R | S | N] DOF ids (a + nmax), then perm (a)
+};
+
+struct BoxRun {     // device-written results per processed box
+  int s, r, n, nq;
+};
+
+struct LevelDev {   // device state of a level
+  const BoxDesc* desc;
+  BoxRun* run;
+  const int* nlist;
+  const int* qlist;
+  const int64_t* pairtab;
+  const int64_t* qpair;
+  int* cur_n;        // current active count per current box
+  const int* cur_off;// offset of a box's act0 in act_dof / act_pos
+  const int* cur_a0; // a0 per current box
+  const int* act_dof;
+  int* act_pos;
+  double2* delta;    // Schur-update pool
+  int* rows;         // int scratch
+  void* Mbuf;        // ID scratch (double2 or float2)
+  double2* Wbuf;
+  double2* arena;    // factor arena (G1, G3, T, Xinv)
+  int* iarena;       // factor int arena (idx)
+  int n_proxy;
+  double proxy_factor;
+  double eps;
+  int* status;
+};
+
+// one per eliminated box, in elimination order (solve plan)
+struct SolveBox {
+  int r, s, n, pad_;
+  const int* idx;          // [R | S | N]
+  const double2* T;  int ldT;
+  const double2* Xinv; int ldX;
+  const double2* XCR; int ldL;   // (s+n) x r
+  const double2* XRC; int ldU;   // r x (s+n)
+};
+
+// ---------------------------------------------------------------------------
+// launch wrappers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// tree.cu
+int gpu_morton_sort(const double* points_rowmajor, int64_t n, const double corner[3],
+                    double side, uint64_t* keys_out_host, int* perm_out_host,
+                    cudaStream_t st);
+// assembly.cu
+void launch_permute_geometry(const double* pts, const double* nrm, const double* w,
+                             const int* perm, int64_t n, double* soa, cudaStream_t st);
+void launch_gather_rows(const LevelDev& L, int b0, int nb, cudaStream_t st);
+void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb,
+                        int mmax_max, bool fp32, cudaStream_t st);
+void launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb,
+                          int amax, int nmax_max, cudaStream_t st);
+struct MergeItem {
+  const double2* src; double2* dst;
+  int ld_src, ld_dst, off_i, off_j, ni, nj;
+  const int* pos_i; const int* pos_j;
+};
+void launch_merge(const MergeItem* items, int nitems, int max_ni, int max_nj,
+                  cudaStream_t st);
+void launch_assemble_root(const Geometry& g, const int* dofs, const int* owner,
+                          const int* pos, const int64_t* pairoff, const int* a0,
+                          int ncur, const double2* delta, int n0, double2* A,
+                          cudaStream_t st);
+void launch_matvec(const Geometry& g, int64_t n, const double2* v, double2* y,
+                   int nrhs, cudaStream_t st);
+// linalg.cu
+void launch_cpqr(const LevelDev& L, int b0, int nb, bool fp32, int amax,
+                 cudaStream_t st);
+void launch_elim_gemms(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                       cudaStream_t st);
+void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
+void launch_schur(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                  cudaStream_t st);
+void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
+                        cudaStream_t st);
+// solve.cu
+void launch_gather_vec(const double2* b, const int* perm, int64_t n, int nrhs,
+                       double2* v, cudaStream_t st);
+void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs,
+                        double2* x, cudaStream_t st);
+void launch_sweep(const SolveBox* boxes, int b0, int nb, int rmax, double2* v,
+                  int64_t n, int nrhs, bool backward, bool adjoint, cudaStream_t st);
+void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n,
+                        int nrhs, double2* vr, cudaStream_t st);
+void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,
+                         int nrhs, double2* v, cudaStream_t st);
+void launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
+                       double2* partial, int nrhs, bool adjoint, cudaStream_t st);
+
+}  // namespace fmmlu
