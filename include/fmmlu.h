@@ -76,6 +76,11 @@ typedef struct fmmlu_opts {
   int precision;              /* FMMLU_PRECISION_*                           */
   double eps_id_divisor;      /* ID tolerance eps_ID = eps / divisor. 1.0    */
   int verbose;                /* 0 quiet, 1 per-level lines on stderr        */
+  int profile;                /* 1: time every kernel launch of the factor
+                                 and of later solves with CUDA events on
+                                 the launching stream and attribute the
+                                 algorithmic flops/bytes to each kernel
+                                 (reported by fmmlu_stats). Default 0.      */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if
@@ -130,9 +135,9 @@ int fmmlu_solve_adjoint(const fmmlu_handle* h, const double* b, double* x,
 
 /* y = A v with A assembled on the fly from the kernel (no factorization; an
  * independent dense product used for residuals). O(N^2) work.
- *   tree : the tree of these points (used only for N); points, normals,
- *          weights as for fmmlu_factor (device); v, y device complex128
- *          N x nrhs column-major, caller order; y must not alias v.
+ *   n    : number of points; points, normals, weights as for fmmlu_factor
+ *          (device, caller order); eta NaN means eta = k;
+ *   v, y : device complex128, N x nrhs column-major; y must not alias v.
  * Errors: INVALID_ARG, CUDA. */
 int fmmlu_matvec(int64_t n, const double* points, const double* normals,
                  const double* weights, double k, double eta, const double* v,
@@ -151,6 +156,14 @@ int fmmlu_stats(const fmmlu_handle* h, char* json, size_t cap);
  * {colour, n_near, near..., n_q, q...}. Returns the number of values needed,
  * or a negative error code. */
 int64_t fmmlu_tree_describe(const fmmlu_tree* t, int64_t* out, int64_t cap);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads, all handles). Never fails. */
+int64_t fmmlu_kernel_launches(void);
+
+/* Clear the per-kernel accounting of a handle created with opts.profile = 1
+ * (so that later solves can be measured alone). Returns 0 or INVALID_ARG. */
+int fmmlu_profile_reset(const fmmlu_handle* h);
 
 /* Free a tree or a factorization handle (either kind; NULL is a no-op). */
 void fmmlu_free(void* tree_or_handle);

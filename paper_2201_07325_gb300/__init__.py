@@ -6,7 +6,8 @@ of include/fmmlu.h; this package is its thin Python binding plus the
 """
 from .binding import (FmmluError, PRECISION_AUTO, PRECISION_FP64, PRECISION_MIXED,  # noqa: F401
                       fmmlu_build_tree, fmmlu_default_opts, fmmlu_factor, fmmlu_free,
-                      fmmlu_last_error, fmmlu_matvec, fmmlu_opts, fmmlu_solve,
+                      fmmlu_kernel_launches, fmmlu_last_error, fmmlu_matvec,
+                      fmmlu_profile_reset, fmmlu_opts, fmmlu_solve,
                       fmmlu_solve_adjoint, fmmlu_stats, fmmlu_tree_describe, load_library,
                       parse_tree_description)
 from .solver import FMMLUSolve, Factorization, fmmlu_solve_autograd  # noqa: F401

@@ -40,6 +40,7 @@ class fmmlu_opts(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("eps_id_divisor", ctypes.c_double),
         ("verbose", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -76,6 +77,10 @@ def load_library(path: str | None = None):
     lib.fmmlu_stats.restype = ci
     lib.fmmlu_tree_describe.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i64]
     lib.fmmlu_tree_describe.restype = i64
+    lib.fmmlu_kernel_launches.argtypes = []
+    lib.fmmlu_kernel_launches.restype = i64
+    lib.fmmlu_profile_reset.argtypes = [vp]
+    lib.fmmlu_profile_reset.restype = ci
     lib.fmmlu_free.argtypes = [vp]
     lib.fmmlu_free.restype = None
     lib.fmmlu_last_error.argtypes = []
@@ -209,6 +214,14 @@ def fmmlu_free(handle):
         load_library().fmmlu_free(handle)
 
 
+def fmmlu_kernel_launches() -> int:
+    return int(load_library().fmmlu_kernel_launches())
+
+
+def fmmlu_profile_reset(handle):
+    _check(load_library().fmmlu_profile_reset(handle))
+
+
 def fmmlu_last_error() -> str:
     return load_library().fmmlu_last_error().decode()
 
@@ -243,6 +256,7 @@ __all__ = [
     "FmmluError", "fmmlu_opts", "load_library", "fmmlu_default_opts", "fmmlu_build_tree",
     "fmmlu_factor", "fmmlu_solve", "fmmlu_solve_adjoint", "fmmlu_matvec", "fmmlu_stats",
     "fmmlu_tree_describe", "fmmlu_free", "fmmlu_last_error", "parse_tree_description",
+    "fmmlu_kernel_launches", "fmmlu_profile_reset",
     "PRECISION_AUTO", "PRECISION_FP64", "PRECISION_MIXED",
 ]
 

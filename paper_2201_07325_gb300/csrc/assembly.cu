@@ -37,7 +37,8 @@ __global__ void k_permute_geometry(const double* __restrict__ pts, const double*
 
 void launch_permute_geometry(const double* pts, const double* nrm, const double* w,
                              const int* perm, int64_t n, double* soa, cudaStream_t st) {
-  k_permute_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, nrm, w, perm, n, soa);
+  FMMLU_LAUNCH("permute_geometry", st,
+               k_permute_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, nrm, w, perm, n, soa));
 }
 
 // ---------------------------------------------------------------------------
@@ -87,7 +88,7 @@ __global__ void k_gather_rows(LevelDev L, int b0) {
 
 void launch_gather_rows(const LevelDev& L, int b0, int nb, cudaStream_t st) {
   if (nb <= 0) return;
-  k_gather_rows<<<nb, 256, 0, st>>>(L, b0);
+  FMMLU_LAUNCH("gather_rows", st, k_gather_rows<<<nb, 256, 0, st>>>(L, b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -156,9 +157,9 @@ void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, in
   if (nb <= 0) return;
   dim3 grid((mmax_max + kIdRows - 1) / kIdRows, nb);
   if (fp32)
-    k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0);
+    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0));
   else
-    k_assemble_id<double2><<<grid, 256, 0, st>>>(L, g, b0);
+    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<double2><<<grid, 256, 0, st>>>(L, g, b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -232,7 +233,7 @@ void launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb, 
   if (nb <= 0) return;
   int64_t total = (int64_t)amax * (amax + nmax_max);
   dim3 grid((unsigned)((total + kElimTile - 1) / kElimTile), 2, nb);
-  k_assemble_elim<<<grid, 256, 0, st>>>(L, g, b0);
+  FMMLU_LAUNCH("assemble_elim", st, k_assemble_elim<<<grid, 256, 0, st>>>(L, g, b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -249,7 +250,7 @@ __global__ void k_merge(const MergeItem* __restrict__ items) {
 
 void launch_merge(const MergeItem* items, int nitems, int, int, cudaStream_t st) {
   if (nitems <= 0) return;
-  k_merge<<<nitems, 256, 0, st>>>(items);
+  FMMLU_LAUNCH("merge", st, k_merge<<<nitems, 256, 0, st>>>(items));
 }
 
 // ---------------------------------------------------------------------------
@@ -279,8 +280,8 @@ void launch_assemble_root(const Geometry& g, const int* dofs, const int* owner, 
                           const double2* delta, int n0, double2* A, cudaStream_t st) {
   if (n0 <= 0) return;
   dim3 grid((n0 + 31) / 32, (n0 + 31) / 32);
-  k_assemble_root<<<grid, dim3(32, 8), 0, st>>>(g, dofs, owner, pos, pairoff, a0, ncur, delta,
-                                                n0, A);
+  FMMLU_LAUNCH("assemble_root", st, k_assemble_root<<<grid, dim3(32, 8), 0, st>>>(
+                                         g, dofs, owner, pos, pairoff, a0, ncur, delta, n0, A));
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +333,7 @@ __global__ void k_matvec(Geometry g, int64_t n, const double2* __restrict__ v,
 void launch_matvec(const Geometry& g, int64_t n, const double2* v, double2* y, int nrhs,
                    cudaStream_t st) {
   dim3 grid((unsigned)((n + 127) / 128), nrhs);
-  k_matvec<<<grid, 128, 0, st>>>(g, n, v, y);
+  FMMLU_LAUNCH("matvec", st, k_matvec<<<grid, 128, 0, st>>>(g, n, v, y));
 }
 
 }  // namespace fmmlu

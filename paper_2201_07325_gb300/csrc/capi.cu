@@ -27,6 +27,7 @@
 
 #include "../../include/fmmlu.h"
 #include "fmmlu_internal.h"
+#include "prof.h"
 #include "tree_host.h"
 
 using namespace fmmlu;
@@ -106,6 +107,7 @@ void default_opts(fmmlu_opts* o) {
   o->precision = FMMLU_PRECISION_AUTO;
   o->eps_id_divisor = 1.0;
   o->verbose = 0;
+  o->profile = 0;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -133,6 +135,9 @@ struct fmmlu_tree {
 
 struct SolveSeg {
   int b0, nb, rmax;
+  double flops_per_rhs;   // algorithmic work of one sweep over this segment
+  double bytes_factor;    // factor bytes read by one sweep
+  double bytes_per_rhs;   // vector bytes read and written per right-hand side
 };
 
 struct fmmlu_handle {
@@ -150,6 +155,8 @@ struct fmmlu_handle {
   std::string stats;
   int64_t factor_entries = 0;  // complex entries of the stored factors (m_f / 16)
   int64_t arena_bytes = 0;
+  bool profile = false;
+  mutable Profiler prof;       // per-kernel accounting (factor + solves)
 };
 
 namespace {
@@ -310,6 +317,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   H->fp32 = opt.precision == FMMLU_PRECISION_MIXED ||
             (opt.precision == FMMLU_PRECISION_AUTO && eps >= 1e-5);
   const double eps_id = eps / opt.eps_id_divisor;
+  H->profile = opt.profile != 0;
+  ProfScope prof_scope(H->profile ? &H->prof : nullptr);
   Timer total_timer;
   DevPool work;   // freed at the end of the factorization
   H->d_perm = H->mem.get<int>((size_t)n);
@@ -464,9 +473,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
       launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
-      launch_elim_gemms(LD, b0, cnt, amax, nmaxm, st);
+      launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st);
+      launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st);
       launch_xrr_inverse(LD, b0, cnt, amax, st);
-      launch_schur(LD, b0, cnt, amax, nmaxm, st);
+      launch_gemm_w(LD, b0, cnt, amax, nmaxm, st);
+      launch_schur_update(LD, b0, cnt, amax, nmaxm, st);
       CK(cudaGetLastError());
     }
     std::vector<BoxRun> run = ddownload(d_run, (size_t)nb, st);
@@ -475,11 +486,36 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     if (int code = status_to_code(status, msg)) throw Error(code, msg + " (level " + std::to_string(lev) + ")");
     L->cur_n = ddownload(L->d_cur_n, L->cur.size(), st);
     L->act_pos = ddownload(L->d_act_pos, L->act_pos.size(), st);
+    if (H->profile) {
+      H->prof.resolve();
+      const double csz = H->fp32 ? 8.0 : 16.0;
+      for (int e = 0; e < nb; ++e) {
+        const BoxDesc& d = desc[e];
+        const BoxRun& rr = run[e];
+        double a = d.a, s_ = rr.s, r_ = rr.r, n_ = rr.n;
+        double m = 2.0 * rr.nq + 2.0 * opt.n_proxy;
+        double qr = 0;
+        for (int j = 0; j < rr.s; ++j) qr += 18.0 * (m - j) * (a - j - 1);
+        qr += 4.0 * s_ * s_ * r_;
+        H->prof.add_work("assemble_id", 0, m * a * csz);
+        H->prof.add_work("cpqr", qr, m * a * csz);
+        if (rr.r == 0) continue;
+        H->prof.add_work("assemble_elim", 0, 2.0 * a * (a + n_) * 16.0);
+        H->prof.add_work("gemm_g1", 8.0 * r_ * (a + n_) * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
+        H->prof.add_work("gemm_g3", 8.0 * (a + n_) * r_ * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
+        H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * s_ + 8.0 * r_ * r_ * r_,
+                         16.0 * (3 * r_ * r_ + r_ * s_));
+        H->prof.add_work("gemm_w", 8.0 * (s_ + n_) * r_ * r_, 16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
+        H->prof.add_work("schur_update", 8.0 * (s_ + n_) * (s_ + n_) * r_,
+                         16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));
+      }
+    }
     // solve plan for this level
     int64_t sum_a = 0, sum_s = 0, max_a = 0, max_r = 0;
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0p = (int)plan.size();
       int rmax = 0;
+      double seg_flops = 0, seg_fbytes = 0, seg_vbytes = 0;
       for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
         const BoxDesc& d = desc[e];
         const BoxRun& rr = run[e];
@@ -497,11 +533,15 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         sb.XRC = d_arena + d.G1_off + rr.s; sb.ldU = d.a;
         plan.push_back(sb);
         rmax = std::max(rmax, rr.r);
+        double ent = (double)rr.s * rr.r + (double)rr.r * rr.r + (double)(rr.s + rr.n) * rr.r;
+        seg_flops += 8.0 * ent;
+        seg_fbytes += 16.0 * ent;
+        seg_vbytes += 16.0 * 2.0 * (rr.r + rr.s + rr.n);
         H->factor_entries += (int64_t)rr.s * rr.r + (int64_t)rr.r * rr.r +
                              2 * (int64_t)(rr.s + rr.n) * rr.r;
       }
       int cnt = (int)plan.size() - b0p;
-      if (cnt > 0) H->segs.push_back({b0p, cnt, rmax});
+      if (cnt > 0) H->segs.push_back({b0p, cnt, rmax, seg_flops, seg_fbytes, seg_vbytes});
     }
     double lms = lt.ms();
     if (opt.verbose)
@@ -548,6 +588,21 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     int status = ddownload(d_status, 1, st)[0];
     std::string msg;
     if (int code = status_to_code(status, msg)) throw Error(code, msg + " (root)");
+    if (H->profile) {
+      H->prof.resolve();
+      double rb = 0;
+      for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
+        double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
+        H->prof.add_work("root_diag", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
+        if (later > 0) {
+          H->prof.add_work("root_w", 8.0 * later * r_ * r_, 16.0 * (2 * later * r_ + r_ * r_));
+          H->prof.add_work("root_schur", 8.0 * later * later * r_,
+                           16.0 * (2 * later * later + 2 * later * r_));
+        }
+        rb += 1;
+      }
+      H->prof.add_work("assemble_root", 0, 16.0 * n0 * (double)n0);
+    }
     H->factor_entries += (int64_t)n0 * n0;
   }
   double root_ms = rt.ms();
@@ -566,6 +621,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
 
 void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, bool adjoint,
                 cudaStream_t st) {
+  ProfScope prof_scope(H->profile ? &H->prof : nullptr);
   int64_t n = H->n;
   DevPool w;
   double2* v = w.get<double2>((size_t)n * nrhs);
@@ -587,6 +643,21 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
   launch_scatter_vec(v, H->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));   // the work buffers are freed on return
+  if (H->profile) {
+    H->prof.resolve();
+    for (const auto& sg : H->segs) {
+      for (const char* nm : {"sweep_fwd", "sweep_bwd"})
+        H->prof.add_work(nm, sg.flops_per_rhs * nrhs, sg.bytes_factor + sg.bytes_per_rhs * nrhs);
+    }
+    int n0 = H->n0;
+    for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
+      double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
+      H->prof.add_work("root_fwd", 8.0 * nrhs * (r_ * r_ + later * r_),
+                       16.0 * (r_ * r_ + later * r_ + 2.0 * nrhs * (later + r_)));
+      H->prof.add_work(later > 0 ? "root_bwd1" : "root_bwd2", 8.0 * nrhs * later * r_,
+                       16.0 * (later * r_ + nrhs * later));
+    }
+  }
 }
 
 }  // namespace
@@ -729,7 +800,12 @@ int fmmlu_matvec(int64_t n, const double* points, const double* normals, const d
 
 int fmmlu_stats(const fmmlu_handle* h, char* json, size_t cap) {
   if (!h || h->magic != kHandleMagic) { g_err = "not a handle"; return FMMLU_ERR_INVALID_ARG; }
-  const std::string& s = h->stats;
+  std::string s = h->stats;
+  if (!s.empty() && s.back() == '}') {
+    s.pop_back();
+    s += ", \"profile\": " + std::string(h->profile ? "true" : "false") +
+         ", \"kernels\": " + h->prof.json() + "}";
+  }
   if (json && cap > 0) {
     size_t m = std::min(cap - 1, s.size());
     std::memcpy(json, s.data(), m);
@@ -763,6 +839,14 @@ int64_t fmmlu_tree_describe(const fmmlu_tree* t, int64_t* out, int64_t cap) {
   }
   if (out) std::memcpy(out, v.data(), sizeof(int64_t) * (size_t)std::min<int64_t>(cap, (int64_t)v.size()));
   return (int64_t)v.size();
+}
+
+int64_t fmmlu_kernel_launches(void) { return launches_total(); }
+
+int fmmlu_profile_reset(const fmmlu_handle* h) {
+  if (!h || h->magic != kHandleMagic) { g_err = "not a handle"; return FMMLU_ERR_INVALID_ARG; }
+  h->prof.reset();
+  return FMMLU_OK;
 }
 
 void fmmlu_free(void* p) {

@@ -97,6 +97,20 @@ struct SolveBox {
 };
 
 // ---------------------------------------------------------------------------
+// launch accounting: every kernel launch of the library goes through
+// FMMLU_LAUNCH, which counts it and, when a profiler is active on the calling
+// thread, brackets it with CUDA events on its stream.
+// ---------------------------------------------------------------------------
+void launch_begin(const char* name, cudaStream_t st);
+void launch_end(const char* name, cudaStream_t st);
+#define FMMLU_LAUNCH(name, st, ...)          \
+  do {                                       \
+    ::fmmlu::launch_begin(name, (st));       \
+    __VA_ARGS__;                             \
+    ::fmmlu::launch_end(name, (st));         \
+  } while (0)
+
+// ---------------------------------------------------------------------------
 // launch wrappers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 // tree.cu
@@ -127,11 +141,15 @@ void launch_matvec(const Geometry& g, int64_t n, const double2* v, double2* y,
 // linalg.cu
 void launch_cpqr(const LevelDev& L, int b0, int nb, bool fp32, int amax,
                  cudaStream_t st);
-void launch_elim_gemms(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                       cudaStream_t st);
+void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                    cudaStream_t st);
+void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                    cudaStream_t st);
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
-void launch_schur(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                  cudaStream_t st);
+void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                   cudaStream_t st);
+void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                         cudaStream_t st);
 void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
                         cudaStream_t st);
 // solve.cu

@@ -184,11 +184,11 @@ void launch_cpqr(const LevelDev& L, int b0, int nb, bool fp32, int amax, cudaStr
   if (fp32) {
     size_t sm = (size_t)amax * (sizeof(float) + sizeof(int));
     cudaFuncSetAttribute(k_cpqr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cpqr<float><<<nb, kQrThreads, sm, st>>>(L, b0);
+    FMMLU_LAUNCH("cpqr", st, k_cpqr<float><<<nb, kQrThreads, sm, st>>>(L, b0));
   } else {
     size_t sm = (size_t)amax * (sizeof(double) + sizeof(int));
     cudaFuncSetAttribute(k_cpqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_cpqr<double><<<nb, kQrThreads, sm, st>>>(L, b0);
+    FMMLU_LAUNCH("cpqr", st, k_cpqr<double><<<nb, kQrThreads, sm, st>>>(L, b0));
   }
 }
 
@@ -378,17 +378,31 @@ static inline unsigned tiles(int m, int n) {
   return (unsigned)(((m + kTile - 1) / kTile) * ((n + kTile - 1) / kTile));
 }
 
-void launch_elim_gemms(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                       cudaStream_t st) {
+void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                    cudaStream_t st) {
   if (nb <= 0) return;
-  k_gemm_g1<<<dim3(tiles(amax, 2 * amax + nmax_max), nb), 256, 0, st>>>(L, b0);
-  k_gemm_g3<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0);
+  FMMLU_LAUNCH("gemm_g1", st,
+               k_gemm_g1<<<dim3(tiles(amax, 2 * amax + nmax_max), nb), 256, 0, st>>>(L, b0));
 }
 
-void launch_schur(const LevelDev& L, int b0, int nb, int amax, int nmax_max, cudaStream_t st) {
+void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                    cudaStream_t st) {
   if (nb <= 0) return;
-  k_gemm_w<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0);
-  k_schur<<<dim3(tiles(amax + nmax_max, amax + nmax_max), nb), 256, 0, st>>>(L, b0);
+  FMMLU_LAUNCH("gemm_g3", st,
+               k_gemm_g3<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0));
+}
+
+void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max, cudaStream_t st) {
+  if (nb <= 0) return;
+  FMMLU_LAUNCH("gemm_w", st,
+               k_gemm_w<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0));
+}
+
+void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
+                         cudaStream_t st) {
+  if (nb <= 0) return;
+  FMMLU_LAUNCH("schur_update", st,
+               k_schur<<<dim3(tiles(amax + nmax_max, amax + nmax_max), nb), 256, 0, st>>>(L, b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -495,7 +509,7 @@ __global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0) {
 
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
   if (nb <= 0) return;
-  k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0);
+  FMMLU_LAUNCH("xrr_inverse", st, k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0));
 }
 
 // ---------------------------------------------------------------------------
@@ -533,11 +547,12 @@ void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
                         cudaStream_t st) {
   for (int i0 = 0; i0 < n0; i0 += nb) {
     int r = std::min(nb, n0 - i0);
-    k_root_diag<<<1, 512, 0, st>>>(A, n0, i0, r, status);
+    FMMLU_LAUNCH("root_diag", st, k_root_diag<<<1, 512, 0, st>>>(A, n0, i0, r, status));
     int later = n0 - i0 - r;
     if (later > 0) {
-      k_root_w<<<tiles(later, r), 256, 0, st>>>(A, n0, i0, r, work);
-      k_root_schur<<<tiles(later, later), 256, 0, st>>>(A, n0, i0, r, work);
+      FMMLU_LAUNCH("root_w", st, k_root_w<<<tiles(later, r), 256, 0, st>>>(A, n0, i0, r, work));
+      FMMLU_LAUNCH("root_schur", st,
+                   k_root_schur<<<tiles(later, later), 256, 0, st>>>(A, n0, i0, r, work));
     }
   }
 }

@@ -1,0 +1,48 @@
+// Per-kernel accounting: launch counts, CUDA-event times on the launching
+// stream, and the algorithmic work (flops, bytes) the host attributes to each
+// kernel class from the sizes it knows after each level.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+namespace fmmlu {
+
+struct ProfEntry {
+  int64_t launches = 0;
+  double ms = 0;      // summed CUDA-event durations
+  double flops = 0;   // algorithmic real flops attributed to these launches
+  double bytes = 0;   // algorithmic DRAM bytes attributed to these launches
+};
+
+struct Profiler {
+  struct Pending {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::map<std::string, ProfEntry> tot;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> spare;
+  cudaEvent_t get();
+  void resolve();     // call after the stream has been synchronised
+  void add_work(const char* name, double flops, double bytes);
+  void reset();
+  std::string json() const;
+  ~Profiler();
+};
+
+extern thread_local Profiler* g_prof;
+int64_t launches_total();
+
+// sets g_prof for a scope
+struct ProfScope {
+  Profiler* saved;
+  explicit ProfScope(Profiler* p) : saved(g_prof) { g_prof = p; }
+  ~ProfScope() { g_prof = saved; }
+};
+
+}  // namespace fmmlu

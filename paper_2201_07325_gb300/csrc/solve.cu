@@ -31,11 +31,11 @@ __global__ void k_scatter_vec(const double2* __restrict__ v, const int* __restri
 }
 void launch_gather_vec(const double2* b, const int* perm, int64_t n, int nrhs, double2* v,
                        cudaStream_t st) {
-  k_gather_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(b, perm, n, v);
+  FMMLU_LAUNCH("gather_vec", st, k_gather_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(b, perm, n, v));
 }
 void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs, double2* x,
                         cudaStream_t st) {
-  k_scatter_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(v, perm, n, x);
+  FMMLU_LAUNCH("scatter_vec", st, k_scatter_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(v, perm, n, x));
 }
 
 // t[k] = sum_j op(M)[k, j] u[j] for k < rows, j < cols, where op(M)[k,j] =
@@ -168,8 +168,9 @@ void launch_sweep(const SolveBox* boxes, int b0, int nb, int rmax, double2* v, i
     cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_sweep<<<dim3(nb, nrhs), 256, sm, st>>>(boxes, b0, v, n, backward ? 1 : 0, adjoint ? 1 : 0,
-                                          rmax);
+  FMMLU_LAUNCH(backward ? "sweep_bwd" : "sweep_fwd", st,
+               k_sweep<<<dim3(nb, nrhs), 256, sm, st>>>(boxes, b0, v, n, backward ? 1 : 0,
+                                                       adjoint ? 1 : 0, rmax));
 }
 
 // ---------------------------------------------------------------------------
@@ -190,12 +191,12 @@ __global__ void k_root_scatter(const double2* __restrict__ vr, const int* __rest
 void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n, int nrhs,
                         double2* vr, cudaStream_t st) {
   if (n0 <= 0) return;
-  k_root_gather<<<dim3((n0 + 255) / 256, nrhs), 256, 0, st>>>(v, dofs, n0, n, vr);
+  FMMLU_LAUNCH("root_gather", st, k_root_gather<<<dim3((n0 + 255) / 256, nrhs), 256, 0, st>>>(v, dofs, n0, n, vr));
 }
 void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n, int nrhs,
                          double2* v, cudaStream_t st) {
   if (n0 <= 0) return;
-  k_root_scatter<<<dim3((n0 + 255) / 256, nrhs), 256, 0, st>>>(vr, dofs, n0, n, v);
+  FMMLU_LAUNCH("root_scatter", st, k_root_scatter<<<dim3((n0 + 255) / 256, nrhs), 256, 0, st>>>(vr, dofs, n0, n, v));
 }
 
 // forward step of block i: z_i = op(D_i^{-1}) b_i (every CTA recomputes it),
@@ -299,7 +300,7 @@ void launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z
     int r = std::min(nb, n0 - i0);
     int later = n0 - i0 - r;
     int nblk = std::max(1, (later + kRootRows - 1) / kRootRows);
-    k_root_fwd<<<dim3(nblk, nrhs), 256, 0, st>>>(A, n0, i0, r, vr, z, adj);
+    FMMLU_LAUNCH("root_fwd", st, k_root_fwd<<<dim3(nblk, nrhs), 256, 0, st>>>(A, n0, i0, r, vr, z, adj));
   }
   // backward: x := z, then blocks from last to first
   int nbl = (n0 + nb - 1) / nb;
@@ -309,10 +310,13 @@ void launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z
     int later = n0 - i0 - r;
     if (later > 0) {
       int nblk = (later + kRootCols - 1) / kRootCols;
-      k_root_bwd1<<<dim3(nblk, nrhs), 256, 0, st>>>(A, n0, i0, r, vr, partial, nblk, adj);
-      k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial, nblk, adj);
+      FMMLU_LAUNCH("root_bwd1", st, k_root_bwd1<<<dim3(nblk, nrhs), 256, 0, st>>>(
+                                        A, n0, i0, r, vr, partial, nblk, adj));
+      FMMLU_LAUNCH("root_bwd2", st, k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial,
+                                                                     nblk, adj));
     } else {
-      k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial, 0, adj);
+      FMMLU_LAUNCH("root_bwd2", st,
+                   k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial, 0, adj));
     }
   }
 }

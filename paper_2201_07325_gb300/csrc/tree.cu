@@ -161,13 +161,14 @@ int gpu_morton_sort(const double* pts, int64_t n, const double corner[3], double
     if ((rc = (int)cudaMalloc(&v0, n * 4))) break;
     if ((rc = (int)cudaMalloc(&v1, n * 4))) break;
     if ((rc = (int)cudaMalloc(&hist, (size_t)16 * nblk * 4))) break;
-    k_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, n, corner[0], corner[1],
-                                                          corner[2], side, k0, v0);
+    FMMLU_LAUNCH("morton", st, k_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                                      pts, n, corner[0], corner[1], corner[2], side, k0, v0));
     for (int pass = 0; pass < 16; ++pass) {
       int shift = 4 * pass;
-      k_radix_hist<<<nblk, kSortThreads, 0, st>>>(k0, n, shift, hist, nblk);
-      k_scan_small<<<1, 1024, 0, st>>>(hist, 16 * nblk);
-      k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(k0, v0, n, shift, hist, nblk, k1, v1);
+      FMMLU_LAUNCH("radix_hist", st, k_radix_hist<<<nblk, kSortThreads, 0, st>>>(k0, n, shift, hist, nblk));
+      FMMLU_LAUNCH("radix_scan", st, k_scan_small<<<1, 1024, 0, st>>>(hist, 16 * nblk));
+      FMMLU_LAUNCH("radix_scatter", st, k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(
+                                             k0, v0, n, shift, hist, nblk, k1, v1));
       std::swap(k0, k1);
       std::swap(v0, v1);
     }
