@@ -81,6 +81,8 @@ typedef struct fmmlu_opts {
                                  the launching stream and attribute the
                                  algorithmic flops/bytes to each kernel
                                  (reported by fmmlu_stats). Default 0.      */
+  int cpqr_single;            /* 1: run every pivoted QR with one CTA per box
+                                 (no row distribution). Default 0.          */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if

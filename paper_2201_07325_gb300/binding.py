@@ -41,6 +41,7 @@ class fmmlu_opts(ctypes.Structure):
         ("eps_id_divisor", ctypes.c_double),
         ("verbose", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("cpqr_single", ctypes.c_int),
     ]
 
 

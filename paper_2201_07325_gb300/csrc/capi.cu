@@ -108,6 +108,7 @@ void default_opts(fmmlu_opts* o) {
   o->eps_id_divisor = 1.0;
   o->verbose = 0;
   o->profile = 0;
+  o->cpqr_single = 0;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -303,6 +304,7 @@ int status_to_code(int s, std::string& msg) {
   if (s & kStatusSingular) { msg = "singular pivot in X_RR or a root block"; return FMMLU_ERR_SINGULAR_PIVOT; }
   if (s & kStatusNonfinite) { msg = "non-finite value in an ID matrix"; return FMMLU_ERR_NONFINITE; }
   if (s & kStatusBound) { msg = "internal size bound exceeded"; return FMMLU_ERR_LIMIT; }
+  if (s & kStatusTimeout) { msg = "a bounded inter-CTA wait gave up"; return FMMLU_ERR_TIMEOUT; }
   return 0;
 }
 
@@ -461,6 +463,53 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     LD.proxy_factor = opt.proxy_radius_factor;
     LD.eps = eps_id;
     LD.status = d_status;
+    // CPQR plan per colour: boxes share the co-resident CTAs in proportion to
+    // their work (rows x a^2); colours with many boxes use one CTA per box.
+    struct ColPlan { int pbeg = 0, np = 0; int64_t scratch = 0; bool dist = false; };
+    std::vector<ColPlan> cplan(seg_start.size());
+    std::vector<CpqrPart> parts;
+    int64_t cpqr_scratch = 0;
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+      int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
+      int amax = 1;
+      for (int e = b0; e < b0 + cnt; ++e) amax = std::max(amax, desc[e].a);
+      int cap = cpqr_dist_capacity(amax, H->fp32);
+      ColPlan& cp = cplan[sgi];
+      if (opt.cpqr_single || cap <= 0 || 2 * cnt > cap) continue;
+      double wsum = 0;
+      std::vector<double> wgt(cnt);
+      for (int e = 0; e < cnt; ++e) {
+        const BoxDesc& d = desc[b0 + e];
+        wgt[e] = (double)d.mmax * d.a * d.a;
+        wsum += wgt[e];
+      }
+      std::vector<int> P(cnt);
+      int tot = 0;
+      for (int e = 0; e < cnt; ++e) {
+        int pmax = std::max(1, std::min(160, desc[b0 + e].mmax / 16));
+        P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * wgt[e] / wsum)));
+        tot += P[e];
+      }
+      while (tot > cap) {
+        int big = (int)(std::max_element(P.begin(), P.end()) - P.begin());
+        if (P[big] <= 1) break;
+        --P[big];
+        --tot;
+      }
+      if (tot > cap) continue;
+      cp.dist = true;
+      cp.pbeg = (int)parts.size();
+      cp.np = tot;
+      int64_t off = 0;
+      for (int e = 0; e < cnt; ++e) {
+        for (int c = 0; c < P[e]; ++c) parts.push_back(CpqrPart{b0 + e, c, P[e], 0, off});
+        off += (int64_t)cpqr_dist_scratch_bytes(P[e], desc[b0 + e].a, H->fp32);
+      }
+      cp.scratch = off;
+      cpqr_scratch = std::max(cpqr_scratch, off);
+    }
+    CpqrPart* d_parts = lw.up(parts, st);
+    unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
       int amax = 1, mmax = 1, nmaxm = 0;
@@ -471,7 +520,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       launch_gather_rows(LD, b0, cnt, st);
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
-      launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
+      if (cplan[sgi].dist) {
+        CK(cudaMemsetAsync(d_cpqr_scratch, 0, (size_t)cplan[sgi].scratch, st));
+        CK(launch_cpqr_dist(LD, d_parts + cplan[sgi].pbeg, cplan[sgi].np, d_cpqr_scratch, amax,
+                            H->fp32, st));
+      } else {
+        launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
+      }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
       launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st);
       launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st);
@@ -503,8 +558,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         H->prof.add_work("assemble_elim", 0, 2.0 * a * (a + n_) * 16.0);
         H->prof.add_work("gemm_g1", 8.0 * r_ * (a + n_) * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
         H->prof.add_work("gemm_g3", 8.0 * (a + n_) * r_ * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
-        H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * s_ + 8.0 * r_ * r_ * r_,
-                         16.0 * (3 * r_ * r_ + r_ * s_));
+        H->prof.add_work("gemm_xrr", 8.0 * r_ * r_ * s_, 16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
+        H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
         H->prof.add_work("gemm_w", 8.0 * (s_ + n_) * r_ * r_, 16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
         H->prof.add_work("schur_update", 8.0 * (s_ + n_) * (s_ + n_) * r_,
                          16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));

@@ -25,6 +25,7 @@ enum StatusBits : int {
   kStatusSingular = 1,
   kStatusNonfinite = 2,
   kStatusBound = 4,      // an internal size bound was exceeded
+  kStatusTimeout = 8,    // a bounded inter-CTA wait gave up
 };
 
 struct Geometry {        // sorted SoA copies of the inputs
@@ -141,6 +142,18 @@ void launch_matvec(const Geometry& g, int64_t n, const double2* v, double2* y,
 // linalg.cu
 void launch_cpqr(const LevelDev& L, int b0, int nb, bool fp32, int amax,
                  cudaStream_t st);
+// cpqr_dist.cu: one box over P cooperating CTAs (cooperative launch)
+struct CpqrPart {
+  int box;       // descriptor index of the box
+  int rank;      // 0 .. P-1
+  int P;         // CTAs of this box
+  int pad_;
+  int64_t scratch_off;   // byte offset of the box's scratch
+};
+size_t cpqr_dist_scratch_bytes(int P, int a, bool fp32);
+int cpqr_dist_capacity(int amax, bool fp32);
+cudaError_t launch_cpqr_dist(const LevelDev& L, const CpqrPart* d_parts, int nparts,
+                             unsigned char* scratch, int amax, bool fp32, cudaStream_t st);
 void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st);
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,

@@ -485,30 +485,40 @@ __device__ void gauss_jordan(double2* X, int r, int64_t ld, int* ipiv, int* stat
   }
 }
 
+// X_RR = (A_RR - T^T A_SR) - X_RS T = G1[s:a, s+n:a+n] - G1[s:a, 0:s] T   (r x r, k = s)
+struct EpiDiff {   // C = Y - acc
+  double2* C; int64_t ldc;
+  const double2* Y; int64_t ldy;
+  __device__ void operator()(int i, int j, double2 v) { C[i + j * ldc] = csub(Y[i + j * ldy], v); }
+};
+
+__global__ void __launch_bounds__(256) k_gemm_xrr(LevelDev L, int b0) {
+  int b = b0 + blockIdx.y;
+  const BoxDesc d = L.desc[b];
+  const BoxRun run = L.run[b];
+  int a = d.a, s = run.s, r = run.r, n = run.n;
+  if (r == 0) return;
+  int tm, tn;
+  if (!tile_of(r, r, tm, tn)) return;
+  const double2* G1 = L.arena + d.G1_off;
+  GemmArgs g{r, r, s, G1 + s, a, L.arena + d.T_off, a};
+  EpiDiff e{L.arena + d.Xinv_off, a, G1 + s + (int64_t)(s + n) * a, a};
+  gemm_tile<false, false>(g, tm, tn, e);
+}
+
 __global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0) {
   extern __shared__ int ipiv[];
   int b = b0 + blockIdx.x;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
-  int a = d.a, s = run.s, r = run.r, n = run.n;
+  int r = run.r;
   if (r == 0) return;
-  const double2* G1 = L.arena + d.G1_off;
-  const double2* T = L.arena + d.T_off;
-  double2* X = L.arena + d.Xinv_off;
-  // X_RR = G1[s:a, s+n:a+n] - G1[s:a, 0:s] T
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    int i = e % r, j = e / r;
-    double2 acc = G1[(s + i) + (int64_t)(s + n + j) * a];
-    double2 sub = mk(0.0, 0.0);
-    for (int l = 0; l < s; ++l) cfma(sub, G1[(s + i) + (int64_t)l * a], T[l + (int64_t)j * a]);
-    X[i + (int64_t)j * a] = csub(acc, sub);
-  }
-  __syncthreads();
-  gauss_jordan(X, r, a, ipiv, L.status);
+  gauss_jordan(L.arena + d.Xinv_off, r, d.a, ipiv, L.status);
 }
 
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
   if (nb <= 0) return;
+  FMMLU_LAUNCH("gemm_xrr", st, k_gemm_xrr<<<dim3(tiles(amax, amax), nb), 256, 0, st>>>(L, b0));
   FMMLU_LAUNCH("xrr_inverse", st, k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0));
 }
 
