@@ -167,6 +167,33 @@ int64_t fmmlu_kernel_launches(void);
  * (so that later solves can be measured alone). Returns 0 or INVALID_ARG. */
 int fmmlu_profile_reset(const fmmlu_handle* h);
 
+/* Size of the fixed device work array used by fmmlu_solve_noalloc. */
+#define FMMLU_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* x = A^{-1} b (adjoint = 0) or x = A^{-H} b (adjoint != 0), the same sweeps
+ * as fmmlu_solve / fmmlu_solve_adjoint, but without allocating any memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc while they solve -- for instance an application whose
+ * device memory is handed out entirely by its own pool allocator (a
+ * cudaMalloc would fail or bypass the pool), or a latency-critical loop that
+ * must not pay the device-wide synchronisation of cudaFree.
+ *   Work space: one fixed device array of FMMLU_NOALLOC_SCRATCH_BYTES (32 MiB)
+ *   compiled into this library; every GPU that loads the library holds it
+ *   until the process exits. A solve needs about 16 * nrhs * (N + 2 n0) bytes
+ *   (n0 from fmmlu_stats); larger requests return FMMLU_ERR_LIMIT and change
+ *   nothing.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Ordering: the call only enqueues work on `stream` and returns; synchronise
+ *   the stream before reading x. All calls share the one array, which keeps
+ *   the last call's contents (nothing in it needs to start at zero): calls on
+ *   one stream are ordered, calls that overlap on the GPU (other streams or
+ *   threads) race.
+ *   b, x, nrhs as for fmmlu_solve. Errors: INVALID_ARG, LIMIT, CUDA. */
+int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, double* x, int nrhs,
+                        int adjoint, void* stream);
+
 /* Free a tree or a factorization handle (either kind; NULL is a no-op). */
 void fmmlu_free(void* tree_or_handle);
 

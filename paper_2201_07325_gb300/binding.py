@@ -82,6 +82,8 @@ def load_library(path: str | None = None):
     lib.fmmlu_kernel_launches.restype = i64
     lib.fmmlu_profile_reset.argtypes = [vp]
     lib.fmmlu_profile_reset.restype = ci
+    lib.fmmlu_solve_noalloc.argtypes = [vp, vp, vp, ci, ci, vp]
+    lib.fmmlu_solve_noalloc.restype = ci
     lib.fmmlu_free.argtypes = [vp]
     lib.fmmlu_free.restype = None
     lib.fmmlu_last_error.argtypes = []
@@ -176,6 +178,19 @@ def fmmlu_solve_adjoint(handle, b: torch.Tensor, x: torch.Tensor, n: int, stream
     return x
 
 
+def fmmlu_solve_noalloc(handle, b: torch.Tensor, x: torch.Tensor, n: int, adjoint: bool = False,
+                        stream=None):
+    """Solve (or adjoint solve) with the library's fixed work array: no
+    device allocation; the call returns once the work is enqueued."""
+    b, nrhs = _cols(b, n, "b")
+    x, nrhs2 = _cols(x, n, "x")
+    if nrhs != nrhs2:
+        raise ValueError("b and x must have the same number of columns")
+    _check(load_library().fmmlu_solve_noalloc(handle, b.data_ptr(), x.data_ptr(), nrhs,
+                                              1 if adjoint else 0, _stream(stream)))
+    return x
+
+
 def fmmlu_matvec(points, normals, weights, k: float, eta: float, v: torch.Tensor,
                  y: torch.Tensor, stream=None):
     n = points.shape[0]
@@ -257,7 +272,7 @@ __all__ = [
     "FmmluError", "fmmlu_opts", "load_library", "fmmlu_default_opts", "fmmlu_build_tree",
     "fmmlu_factor", "fmmlu_solve", "fmmlu_solve_adjoint", "fmmlu_matvec", "fmmlu_stats",
     "fmmlu_tree_describe", "fmmlu_free", "fmmlu_last_error", "parse_tree_description",
-    "fmmlu_kernel_launches", "fmmlu_profile_reset",
+    "fmmlu_kernel_launches", "fmmlu_profile_reset", "fmmlu_solve_noalloc",
     "PRECISION_AUTO", "PRECISION_FP64", "PRECISION_MIXED",
 ]
 

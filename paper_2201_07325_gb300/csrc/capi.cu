@@ -18,6 +18,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <sstream>
 #include <stdexcept>
@@ -920,3 +921,80 @@ void fmmlu_free(void* p) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without allocating. Some callers cannot call cudaMalloc while they
+// solve: an application whose device memory is handed out entirely by its
+// own pool allocator (a cudaMalloc would fail or bypass the pool), or a
+// latency-critical loop that must not pay the device-wide synchronisation of
+// cudaFree. For them the work vectors of a solve live in one fixed device
+// array that is part of this library. Every GPU that loads the library holds
+// the array until the process exits. The host cannot use the array's name as
+// a device address, so the address is looked up once per device, with that
+// device current, by cudaGetSymbolAddress on the first call.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FMMLU_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+unsigned char* noalloc_scratch_for_current_device() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices)
+    throw Error(FMMLU_ERR_LIMIT, "device ordinal above 63 for the fixed work array");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+inline size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, double* x, int nrhs,
+                                   int adjoint, void* stream) {
+  return guard([&] {
+    if (!h || h->magic != kHandleMagic || !b || !x || nrhs < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->n;
+    const int n0 = h->n0;
+    const int nblk = std::max(1, (n0 + 511) / 512);
+    const size_t bv = round256((size_t)16 * n * nrhs);
+    const size_t br = round256((size_t)16 * n0 * nrhs);
+    const size_t bp = round256((size_t)16 * nrhs * nblk * 256);
+    const size_t need = bv + 2 * br + bp;
+    if (need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
+      throw Error(FMMLU_ERR_LIMIT,
+                  "fmmlu_solve_noalloc needs " + std::to_string(need) +
+                      " bytes of work space; the fixed array holds " +
+                      std::to_string((size_t)FMMLU_NOALLOC_SCRATCH_BYTES));
+    unsigned char* base = noalloc_scratch_for_current_device();
+    double2* v = reinterpret_cast<double2*>(base);
+    double2* vr = reinterpret_cast<double2*>(base + bv);
+    double2* z = reinterpret_cast<double2*>(base + bv + br);
+    double2* partial = reinterpret_cast<double2*>(base + bv + 2 * br);
+    const bool adj = adjoint != 0;
+    launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, v, st);
+    for (const auto& sg : h->segs)
+      launch_sweep(h->d_boxes, sg.b0, sg.nb, sg.rmax, v, n, nrhs, false, adj, st);
+    if (n0 > 0) {
+      launch_root_gather(v, h->d_root_dofs, n0, n, nrhs, vr, st);
+      launch_root_solve(h->d_root, n0, h->nb_root, vr, z, partial, nrhs, adj, st);
+      launch_root_scatter(vr, h->d_root_dofs, n0, n, nrhs, v, st);
+    }
+    for (auto it = h->segs.rbegin(); it != h->segs.rend(); ++it)
+      launch_sweep(h->d_boxes, it->b0, it->nb, it->rmax, v, n, nrhs, true, adj, st);
+    launch_scatter_vec(v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
+    CK(cudaGetLastError());
+  });
+}
