@@ -179,9 +179,10 @@ int fmmlu_profile_reset(const fmmlu_handle* h);
  * must not pay the device-wide synchronisation of cudaFree.
  *   Work space: one fixed device array of FMMLU_NOALLOC_SCRATCH_BYTES (32 MiB)
  *   compiled into this library; every GPU that loads the library holds it
- *   until the process exits. A solve needs about 16 * nrhs * (N + 2 n0) bytes
- *   (n0 from fmmlu_stats); larger requests return FMMLU_ERR_LIMIT and change
- *   nothing.
+ *   until the process exits. A solve needs about 16 * nrhs * (N + 2 n0 + p)
+ *   bytes (n0 from fmmlu_stats; p, the partial sums of one colour of the
+ *   backward sweep, is at most a few times n0); larger requests return
+ *   FMMLU_ERR_LIMIT and change nothing.
  *   Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.

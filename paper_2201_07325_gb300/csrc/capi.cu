@@ -135,13 +135,6 @@ struct fmmlu_tree {
   ~fmmlu_tree() { if (d_perm) cudaFree(d_perm); }
 };
 
-struct SolveSeg {
-  int b0, nb, rmax;
-  double flops_per_rhs;   // algorithmic work of one sweep over this segment
-  double bytes_factor;    // factor bytes read by one sweep
-  double bytes_per_rhs;   // vector bytes read and written per right-hand side
-};
-
 struct fmmlu_handle {
   uint32_t magic = kHandleMagic;
   int64_t n = 0;
@@ -150,7 +143,9 @@ struct fmmlu_handle {
   DevPool mem;                 // factors, plans, permutation
   int* d_perm = nullptr;
   SolveBox* d_boxes = nullptr;
-  std::vector<SolveSeg> segs;  // elimination order
+  SweepItem* d_items = nullptr;
+  std::vector<SweepSeg> segs;  // elimination order
+  int64_t part_max = 0;        // partial sums per right-hand side (backward sweep)
   int n0 = 0, nb_root = 64;
   int* d_root_dofs = nullptr;
   double2* d_root = nullptr;
@@ -339,6 +334,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
      << ", \"precision\": \"" << (H->fp32 ? "mixed" : "fp64") << "\", \"nlevels\": " << T.nlevels
      << ", \"levels\": [";
   std::vector<SolveBox> plan;
+  std::vector<SweepItem> items;
   std::unique_ptr<LevelState> prev;
   int root_level = 1;
   bool first_level = true;
@@ -487,7 +483,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       std::vector<int> P(cnt);
       int tot = 0;
       for (int e = 0; e < cnt; ++e) {
-        int pmax = std::max(1, std::min(160, desc[b0 + e].mmax / 16));
+        int pmax = std::max(1, std::min(160, desc[b0 + e].mmax / 64));
         P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * wgt[e] / wsum)));
         tot += P[e];
       }
@@ -509,8 +505,48 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       cp.scratch = off;
       cpqr_scratch = std::max(cpqr_scratch, off);
     }
+    // Gauss-Jordan plan: CTAs in proportion to a^3 (r is only known on the
+    // device; a bounds it), at least 16 columns per CTA.
+    std::vector<ColPlan> gplan(seg_start.size());
+    int64_t gj_scratch = 0;
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+      int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
+      int amax = 1;
+      for (int e = b0; e < b0 + cnt; ++e) amax = std::max(amax, desc[e].a);
+      int cap = gj_dist_capacity(amax);
+      ColPlan& gp = gplan[sgi];
+      if (opt.cpqr_single || cap <= 0 || 2 * cnt > cap || amax < 32) continue;
+      double wsum = 0;
+      for (int e = b0; e < b0 + cnt; ++e) wsum += std::pow((double)desc[e].a, 3.0);
+      std::vector<int> P(cnt);
+      int tot = 0;
+      for (int e = 0; e < cnt; ++e) {
+        double a3 = std::pow((double)desc[b0 + e].a, 3.0);
+        int pmax = std::max(1, desc[b0 + e].a / 16);
+        P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * a3 / wsum)));
+        tot += P[e];
+      }
+      while (tot > cap) {
+        int big = (int)(std::max_element(P.begin(), P.end()) - P.begin());
+        if (P[big] <= 1) break;
+        --P[big];
+        --tot;
+      }
+      if (tot > cap) continue;
+      gp.dist = true;
+      gp.pbeg = (int)parts.size();
+      gp.np = tot;
+      int64_t off = 0;
+      for (int e = 0; e < cnt; ++e) {
+        for (int q = 0; q < P[e]; ++q) parts.push_back(CpqrPart{b0 + e, q, P[e], 0, off});
+        off += (int64_t)gj_dist_scratch_bytes(desc[b0 + e].a);
+      }
+      gp.scratch = off;
+      gj_scratch = std::max(gj_scratch, off);
+    }
     CpqrPart* d_parts = lw.up(parts, st);
     unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
+    unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
       int amax = 1, mmax = 1, nmaxm = 0;
@@ -531,7 +567,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
       launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st);
       launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st);
-      launch_xrr_inverse(LD, b0, cnt, amax, st);
+      launch_gemm_xrr(LD, b0, cnt, amax, st);
+      if (gplan[sgi].dist) {
+        CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
+        CK(launch_gj_dist(LD, d_parts + gplan[sgi].pbeg, gplan[sgi].np, d_gj_scratch, amax, st));
+      } else {
+        launch_xrr_inverse(LD, b0, cnt, amax, st);
+      }
       launch_gemm_w(LD, b0, cnt, amax, nmaxm, st);
       launch_schur_update(LD, b0, cnt, amax, nmaxm, st);
       CK(cudaGetLastError());
@@ -570,8 +612,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     int64_t sum_a = 0, sum_s = 0, max_a = 0, max_r = 0;
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0p = (int)plan.size();
-      int rmax = 0;
-      double seg_flops = 0, seg_fbytes = 0, seg_vbytes = 0;
+      int i0p = (int)items.size();
+      int rmax = 0, smax = 0;
+      int64_t part = 0;
+      double fc = 0, bc = 0, fb = 0, bb = 0, seg_vbytes = 0;
       for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
         const BoxDesc& d = desc[e];
         const BoxRun& rr = run[e];
@@ -587,17 +631,35 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         sb.Xinv = d_arena + d.Xinv_off; sb.ldX = d.a;
         sb.XCR = d_arena + d.G3_off + (int64_t)rr.s * ld3; sb.ldL = (int)ld3;
         sb.XRC = d_arena + d.G1_off + rr.s; sb.ldU = d.a;
+        sb.item_beg = (int)items.size();
+        for (int c0 = 0; c0 < rr.s + rr.n; c0 += kSweepChunk) {
+          items.push_back(SweepItem{(int)plan.size(), c0, std::min(rr.s + rr.n, c0 + kSweepChunk),
+                                    (int)part});
+          part += rr.r;
+        }
+        sb.item_cnt = (int)items.size() - sb.item_beg;
         plan.push_back(sb);
         rmax = std::max(rmax, rr.r);
-        double ent = (double)rr.s * rr.r + (double)rr.r * rr.r + (double)(rr.s + rr.n) * rr.r;
-        seg_flops += 8.0 * ent;
-        seg_fbytes += 16.0 * ent;
+        smax = std::max(smax, rr.s);
+        double ec = (double)(rr.s + rr.n) * rr.r;
+        double eb = (double)rr.s * rr.r + (double)rr.r * rr.r;
+        fc += 8.0 * ec; bc += 16.0 * ec;
+        fb += 8.0 * eb; bb += 16.0 * eb;
         seg_vbytes += 16.0 * 2.0 * (rr.r + rr.s + rr.n);
         H->factor_entries += (int64_t)rr.s * rr.r + (int64_t)rr.r * rr.r +
                              2 * (int64_t)(rr.s + rr.n) * rr.r;
       }
       int cnt = (int)plan.size() - b0p;
-      if (cnt > 0) H->segs.push_back({b0p, cnt, rmax, seg_flops, seg_fbytes, seg_vbytes});
+      if (cnt > 0) {
+        SweepSeg sg;
+        sg.b0 = b0p; sg.nb = cnt;
+        sg.i0 = i0p; sg.ni = (int)items.size() - i0p;
+        sg.rmax = rmax; sg.smax = smax; sg.part = part;
+        sg.flops_c = fc; sg.bytes_c = bc; sg.flops_b = fb; sg.bytes_b = bb;
+        sg.bytes_per_rhs = seg_vbytes;
+        H->segs.push_back(sg);
+        H->part_max = std::max(H->part_max, part);
+      }
     }
     double lms = lt.ms();
     if (opt.verbose)
@@ -663,6 +725,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   }
   double root_ms = rt.ms();
   H->d_boxes = H->mem.up(plan, st);
+  H->d_items = H->mem.up(items, st);
   CK(cudaStreamSynchronize(st));
   double tot_ms = total_timer.ms();
   if (opt.verbose)
@@ -681,9 +744,11 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
   int64_t n = H->n;
   DevPool w;
   double2* v = w.get<double2>((size_t)n * nrhs);
+  const int64_t pst = std::max<int64_t>(1, H->part_max);
+  double2* part = w.get<double2>((size_t)pst * nrhs);
   launch_gather_vec(reinterpret_cast<const double2*>(b), H->d_perm, n, nrhs, v, st);
   for (const auto& sg : H->segs)
-    launch_sweep(H->d_boxes, sg.b0, sg.nb, sg.rmax, v, n, nrhs, false, adjoint, st);
+    launch_sweep(H->d_boxes, H->d_items, sg, v, n, nrhs, false, adjoint, part, pst, st);
   if (H->n0 > 0) {
     int n0 = H->n0;
     double2* vr = w.get<double2>((size_t)n0 * nrhs);
@@ -695,15 +760,17 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
     launch_root_scatter(vr, H->d_root_dofs, n0, n, nrhs, v, st);
   }
   for (auto it = H->segs.rbegin(); it != H->segs.rend(); ++it)
-    launch_sweep(H->d_boxes, it->b0, it->nb, it->rmax, v, n, nrhs, true, adjoint, st);
+    launch_sweep(H->d_boxes, H->d_items, *it, v, n, nrhs, true, adjoint, part, pst, st);
   launch_scatter_vec(v, H->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));   // the work buffers are freed on return
   if (H->profile) {
     H->prof.resolve();
     for (const auto& sg : H->segs) {
-      for (const char* nm : {"sweep_fwd", "sweep_bwd"})
-        H->prof.add_work(nm, sg.flops_per_rhs * nrhs, sg.bytes_factor + sg.bytes_per_rhs * nrhs);
+      H->prof.add_work("sweep_fwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
+      H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+      H->prof.add_work("sweep_bwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
+      H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
     }
     int n0 = H->n0;
     for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
@@ -972,7 +1039,9 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
     const size_t bv = round256((size_t)16 * n * nrhs);
     const size_t br = round256((size_t)16 * n0 * nrhs);
     const size_t bp = round256((size_t)16 * nrhs * nblk * 256);
-    const size_t need = bv + 2 * br + bp;
+    const int64_t pst = std::max<int64_t>(1, h->part_max);
+    const size_t bs = round256((size_t)16 * nrhs * pst);
+    const size_t need = bv + 2 * br + bp + bs;
     if (need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
       throw Error(FMMLU_ERR_LIMIT,
                   "fmmlu_solve_noalloc needs " + std::to_string(need) +
@@ -983,17 +1052,18 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
     double2* vr = reinterpret_cast<double2*>(base + bv);
     double2* z = reinterpret_cast<double2*>(base + bv + br);
     double2* partial = reinterpret_cast<double2*>(base + bv + 2 * br);
+    double2* spart = reinterpret_cast<double2*>(base + bv + 2 * br + bp);
     const bool adj = adjoint != 0;
     launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, v, st);
     for (const auto& sg : h->segs)
-      launch_sweep(h->d_boxes, sg.b0, sg.nb, sg.rmax, v, n, nrhs, false, adj, st);
+      launch_sweep(h->d_boxes, h->d_items, sg, v, n, nrhs, false, adj, spart, pst, st);
     if (n0 > 0) {
       launch_root_gather(v, h->d_root_dofs, n0, n, nrhs, vr, st);
       launch_root_solve(h->d_root, n0, h->nb_root, vr, z, partial, nrhs, adj, st);
       launch_root_scatter(vr, h->d_root_dofs, n0, n, nrhs, v, st);
     }
     for (auto it = h->segs.rbegin(); it != h->segs.rend(); ++it)
-      launch_sweep(h->d_boxes, it->b0, it->nb, it->rmax, v, n, nrhs, true, adj, st);
+      launch_sweep(h->d_boxes, h->d_items, *it, v, n, nrhs, true, adj, spart, pst, st);
     launch_scatter_vec(v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
     CK(cudaGetLastError());
   });

@@ -19,48 +19,11 @@
 #include <algorithm>
 #include <vector>
 
-#include "device_common.cuh"
+#include "coop.cuh"
 
 namespace fmmlu {
 
 constexpr int kDistThreads = 256;
-constexpr long long kSpinLimit = 20000000;   // ~2 s at 100 ns per poll
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// returns false when the box was aborted (timeout here or in another CTA)
-__device__ bool box_barrier(unsigned* ctr, unsigned target, int* abort_flag, int* status) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    atomicAdd(ctr, 1u);
-    long long spins = 0;
-    while (ld_acquire_u32(ctr) < target) {
-      if (ld_acquire_u32(reinterpret_cast<unsigned*>(abort_flag))) { ok = 0; break; }
-      if (++spins > kSpinLimit) {
-        atomicExch(abort_flag, 1);
-        set_status(status, kStatusTimeout);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <typename T> __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
-template <typename T> __device__ __forceinline__ void stcg(T* p, T v) { __stcg(p, v); }
-
 template <typename Rl>
 __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
                                                             const CpqrPart* __restrict__ parts,
@@ -91,7 +54,7 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
   __shared__ C s_v0, s_alpha;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const Rl eps = (Rl)L.eps;
-  const int chunk = (m + P - 1) / P;
+  const int chunk = ((m + P - 1) / P + 31) & ~31;   // whole warps of rows
   const int r0 = min(m, rank * chunk), r1 = min(m, r0 + chunk);
   unsigned nbar = 0;
 #define BARRIER()                                                                   \
@@ -103,7 +66,7 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
   for (int k = tid; k < a; k += blockDim.x) perm[k] = k;
   for (int k = warp; k < a; k += nw) {
     Rl acc = 0;
-    for (int i = r0 + lane; i < r1; i += 32) acc += cabs2(M[i + k * ld]);
+    for (int i = r0 + lane; i < r1; i += 32) cnorm_acc(acc, M[i + k * ld]);
     acc = warp_sum(acc);
     if (lane == 0) stcg(part_norm + (int64_t)rank * a + k, acc);
   }
@@ -203,9 +166,10 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
       const C tw = w[k];
       Rl acc = 0;
       for (int i = lo + lane; i < r1; i += 32) {
-        C t = csub(M[i + k * ld], cmul(M[i + j * ld], tw));
+        C t = M[i + k * ld];
+        cfms(t, M[i + j * ld], tw);
         M[i + k * ld] = t;
-        acc += cabs2(t);
+        cnorm_acc(acc, t);
       }
       acc = warp_sum(acc);
       if (lane == 0) stcg(part_norm + (int64_t)rank * a + k, acc);

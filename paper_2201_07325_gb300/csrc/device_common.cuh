@@ -39,6 +39,15 @@ __host__ __device__ __forceinline__ void cfma_cj(double2& acc, double2 a, double
   acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
 }
+// acc -= a * b (four fused multiply-adds)
+__host__ __device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += |a|^2 (two fused multiply-adds)
+__host__ __device__ __forceinline__ void cnorm_acc(double& acc, double2 a) {
+  acc = fma(a.x, a.x, acc); acc = fma(a.y, a.y, acc);
+}
 __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   double d = b.x * b.x + b.y * b.y;
   return mk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
@@ -59,6 +68,13 @@ __host__ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 __host__ __device__ __forceinline__ void cfma_cj(float2& acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
   acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ void cfms(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(-a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(-a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ void cnorm_acc(float& acc, float2 a) {
+  acc = fmaf(a.x, a.x, acc); acc = fmaf(a.y, a.y, acc);
 }
 __host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
   float d = b.x * b.x + b.y * b.y;

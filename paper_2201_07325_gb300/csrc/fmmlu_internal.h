@@ -90,11 +90,30 @@ struct LevelDev {   // device state of a level
 // one per eliminated box, in elimination order (solve plan)
 struct SolveBox {
   int r, s, n, pad_;
+  int item_beg, item_cnt;  // chunks of C = [S | N] (SweepItem list)
   const int* idx;          // [R | S | N]
   const double2* T;  int ldT;
   const double2* Xinv; int ldX;
   const double2* XCR; int ldL;   // (s+n) x r
   const double2* XRC; int ldU;   // r x (s+n)
+};
+
+// a chunk [c0, c1) of a box's C rows (forward) or columns (backward)
+constexpr int kSweepChunk = 256;
+struct SweepItem {
+  int box;       // index into the SolveBox array
+  int c0, c1;
+  int part;      // offset of this chunk's r partial sums (per right-hand side)
+};
+// one colour of one level in the solve plan
+struct SweepSeg {
+  int b0, nb;    // boxes [b0, b0 + nb) of the SolveBox array
+  int i0, ni;    // items [i0, i0 + ni)
+  int rmax, smax;
+  int64_t part;  // partial sums needed per right-hand side
+  double flops_c, bytes_c;   // per sweep: X_CR / X_RC products (per rhs: flops)
+  double flops_b, bytes_b;   // per sweep: T and X_RR^{-1} products
+  double bytes_per_rhs;      // vector bytes read and written per right-hand side
 };
 
 // ---------------------------------------------------------------------------
@@ -154,10 +173,16 @@ size_t cpqr_dist_scratch_bytes(int P, int a, bool fp32);
 int cpqr_dist_capacity(int amax, bool fp32);
 cudaError_t launch_cpqr_dist(const LevelDev& L, const CpqrPart* d_parts, int nparts,
                              unsigned char* scratch, int amax, bool fp32, cudaStream_t st);
+// gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
+size_t gj_dist_scratch_bytes(int a);
+int gj_dist_capacity(int amax);
+cudaError_t launch_gj_dist(const LevelDev& L, const CpqrPart* d_parts, int nparts,
+                           unsigned char* scratch, int amax, cudaStream_t st);
 void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st);
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st);
+void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
 void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                    cudaStream_t st);
@@ -170,8 +195,9 @@ void launch_gather_vec(const double2* b, const int* perm, int64_t n, int nrhs,
                        double2* v, cudaStream_t st);
 void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs,
                         double2* x, cudaStream_t st);
-void launch_sweep(const SolveBox* boxes, int b0, int nb, int rmax, double2* v,
-                  int64_t n, int nrhs, bool backward, bool adjoint, cudaStream_t st);
+void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
+                  double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
+                  double2* partial, int64_t pstride, cudaStream_t st);
 void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n,
                         int nrhs, double2* vr, cudaStream_t st);
 void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,

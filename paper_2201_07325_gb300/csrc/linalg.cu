@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kQrThreads) k_cpqr(LevelDev L, int b0) {
   for (int k = tid; k < a; k += blockDim.x) perm[k] = k;
   for (int k = warp; k < a; k += nw) {
     Rl acc = 0;
-    for (int i = lane; i < m; i += 32) acc += cabs2(M[i + k * ld]);
+    for (int i = lane; i < m; i += 32) cnorm_acc(acc, M[i + k * ld]);
     acc = warp_sum(acc);
     if (lane == 0) norms[k] = acc;
   }
@@ -126,10 +126,9 @@ __global__ void __launch_bounds__(kQrThreads) k_cpqr(LevelDev L, int b0) {
       }
       for (int i = j + 1 + lane; i < m; i += 32) {
         C t = M[i + k * ld];
-        C u = cmul(M[i + j * ld], tw);
-        t = csub(t, u);
+        cfms(t, M[i + j * ld], tw);
         M[i + k * ld] = t;
-        acc += cabs2(t);
+        cnorm_acc(acc, t);
       }
       acc = warp_sum(acc);
       if (lane == 0) norms[k] = acc;
@@ -462,7 +461,9 @@ __device__ void gauss_jordan(double2* X, int r, int64_t ld, int* ipiv, int* stat
       int i = e % r, c = e / r;
       if (i == j || c == j) continue;
       double2 f = X[i + j * ld];
-      X[i + c * ld] = csub(X[i + c * ld], cmul(f, X[j + c * ld]));
+      double2 xv = X[i + c * ld];
+      cfms(xv, f, X[j + c * ld]);
+      X[i + c * ld] = xv;
     }
     __syncthreads();
     for (int i = tid; i < r; i += blockDim.x) {
@@ -516,9 +517,13 @@ __global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0) {
   gauss_jordan(L.arena + d.Xinv_off, r, d.a, ipiv, L.status);
 }
 
-void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
+void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
   if (nb <= 0) return;
   FMMLU_LAUNCH("gemm_xrr", st, k_gemm_xrr<<<dim3(tiles(amax, amax), nb), 256, 0, st>>>(L, b0));
+}
+
+void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
+  if (nb <= 0) return;
   FMMLU_LAUNCH("xrr_inverse", st, k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0));
 }
 

@@ -38,139 +38,180 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs, 
   FMMLU_LAUNCH("scatter_vec", st, k_scatter_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(v, perm, n, x));
 }
 
-// t[k] = sum_j op(M)[k, j] u[j] for k < rows, j < cols, where op(M)[k,j] =
-// M[k + j ld] (conj = false) or conj(M[j + k ld]) (transposed-conjugated).
-// Result in shared t[]; all threads of the block participate.
-template <bool CONJT>
-__device__ void block_matvec_red(const double2* __restrict__ M, int64_t ld, int rows, int cols,
-                                 const double2* u_sh, double2* t, double2* red) {
+// Box sweeps, two launches per colour and direction:
+//   forward:  k_fwd_z (one CTA per box)   z = op(X_RR^{-1}) (b_R - op(T)^T b_S), b_R = z
+//             k_fwd_c (one CTA per chunk) b_C -= op(X_CR) z over a chunk of C rows
+//   backward: k_bwd_t (one CTA per chunk) partial = op(X_RC) x_C over a chunk of C
+//             k_bwd_x (one CTA per box)   x_R -= op(X_RR^{-1}) sum(partials); x_S -= op(T) x_R
+// op() is the identity for A^{-1}; for A^{-H} the roles are (X_RC^H, X_CR^H,
+// X_RR^{-H}, conj(T)). Chunks let one large box use many SMs.
+
+__global__ void __launch_bounds__(256) k_fwd_z(const SolveBox* __restrict__ boxes, int b0,
+                                               double2* __restrict__ v, int64_t n, int adjoint) {
+  extern __shared__ double2 sh[];
+  const SolveBox B = boxes[b0 + blockIdx.x];
+  const int r = B.r, s = B.s;
+  double2* vc = v + blockIdx.y * n;
+  double2* bR = sh;                 // r
+  double2* bS = sh + B.r;           // s
+  const int* Ridx = B.idx;
+  const int* Sidx = B.idx + r;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) bS[i] = vc[Sidx[i]];
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    double2 acc = vc[Ridx[k]];
+    const double2* Tk = B.T + (int64_t)k * B.ldT;
+    for (int i = 0; i < s; ++i) {
+      double2 tv = adjoint ? cconj(Tk[i]) : Tk[i];
+      cfms(acc, tv, bS[i]);
+    }
+    bR[k] = acc;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    double2 acc = mk(0.0, 0.0);
+    if (!adjoint)
+      for (int l = 0; l < r; ++l) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], bR[l]);
+    else
+      for (int l = 0; l < r; ++l) cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], bR[l]);
+    vc[Ridx[k]] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxes,
+                                               const SweepItem* __restrict__ items, int i0,
+                                               double2* __restrict__ v, int64_t n, int adjoint) {
+  extern __shared__ double2 z[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  const int r = B.r;
+  double2* vc = v + blockIdx.y * n;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) z[k] = vc[B.idx[k]];
+  __syncthreads();
+  const int* Cidx = B.idx + r;
+  for (int i = it.c0 + threadIdx.x; i < it.c1; i += blockDim.x) {
+    double2 acc = mk(0.0, 0.0);
+    if (!adjoint)
+      for (int k = 0; k < r; ++k) cfma(acc, B.XCR[i + (int64_t)k * B.ldL], z[k]);
+    else
+      for (int k = 0; k < r; ++k) cfma_cj(acc, B.XRC[k + (int64_t)i * B.ldU], z[k]);
+    int dof = Cidx[i];
+    vc[dof] = csub(vc[dof], acc);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxes,
+                                               const SweepItem* __restrict__ items, int i0,
+                                               const double2* __restrict__ v, int64_t n,
+                                               double2* __restrict__ partial, int64_t pstride,
+                                               int adjoint) {
+  extern __shared__ double2 sh[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  const int r = B.r;
+  const double2* vc = v + blockIdx.y * n;
+  const int w = it.c1 - it.c0;
+  double2* u = sh;            // chunk values of x_C
+  double2* red = sh + w;      // 256
+  const int* Cidx = B.idx + r;
+  for (int j = threadIdx.x; j < w; j += blockDim.x) u[j] = vc[Cidx[it.c0 + j]];
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int kb = 0; kb < rows; kb += 32) {
+  double2* out = partial + blockIdx.y * pstride + it.part;
+  for (int kb = 0; kb < r; kb += 32) {
     int k = kb + lane;
     double2 acc = mk(0.0, 0.0);
-    if (k < rows) {
-      for (int j = warp; j < cols; j += nw) {
-        if (!CONJT) cfma(acc, M[k + j * ld], u_sh[j]);
-        else cfma_cj(acc, M[j + (int64_t)k * ld], u_sh[j]);
-      }
+    if (k < r) {
+      if (!adjoint)
+        for (int j = warp; j < w; j += nw)
+          cfma(acc, B.XRC[k + (int64_t)(it.c0 + j) * B.ldU], u[j]);
+      else
+        for (int j = warp; j < w; j += nw)
+          cfma_cj(acc, B.XCR[(it.c0 + j) + (int64_t)k * B.ldL], u[j]);
     }
     red[warp * 32 + lane] = acc;
     __syncthreads();
-    if (warp == 0) {
-      double2 s = mk(0.0, 0.0);
-      for (int w = 0; w < nw; ++w) s = cadd(s, red[w * 32 + lane]);
-      if (k < rows) t[k] = s;
+    if (warp == 0 && k < r) {
+      double2 t = mk(0.0, 0.0);
+      for (int q = 0; q < nw; ++q) t = cadd(t, red[q * 32 + lane]);
+      out[k] = t;
     }
     __syncthreads();
   }
 }
 
-// Box sweep. Shared memory: bR, z (rmax each), u (rmax + s + n capped: we
-// stage the gathered C-part in chunks through global reads instead).
-__global__ void __launch_bounds__(256) k_sweep(const SolveBox* __restrict__ boxes, int b0,
-                                               double2* __restrict__ v, int64_t n, int backward,
-                                               int adjoint, int rmax) {
+__global__ void __launch_bounds__(256) k_bwd_x(const SolveBox* __restrict__ boxes, int b0,
+                                               const SweepItem* __restrict__ items,
+                                               double2* __restrict__ v, int64_t n,
+                                               const double2* __restrict__ partial,
+                                               int64_t pstride, int adjoint) {
   extern __shared__ double2 sh[];
   const SolveBox B = boxes[b0 + blockIdx.x];
-  const int r = B.r, s = B.s, nn = B.n;
-  if (r == 0) return;
-  const int c = blockIdx.y;
-  double2* vc = v + c * n;
-  double2* t1 = sh;              // rmax
-  double2* t2 = sh + rmax;       // rmax
-  double2* red = sh + 2 * rmax;  // 256
-  double2* u = red + 256;        // staging for gathered vectors (rmax + chunk)
+  const int r = B.r, s = B.s;
+  double2* vc = v + blockIdx.y * n;
+  const double2* pc = partial + blockIdx.y * pstride;
+  double2* t = sh;        // r
+  double2* xr = sh + r;   // r
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    double2 acc = mk(0.0, 0.0);
+    for (int q = B.item_beg; q < B.item_beg + B.item_cnt; ++q) acc = cadd(acc, pc[items[q].part + k]);
+    t[k] = acc;
+  }
+  __syncthreads();
   const int* Ridx = B.idx;
   const int* Sidx = B.idx + r;
-  const int* Cidx = B.idx + r;   // C = [S | N]
-  const int tid = threadIdx.x;
-  const int m = s + nn;
-  if (!backward) {
-    // t1 = b_R - op(T)^T b_S
-    for (int k = tid; k < r; k += blockDim.x) {
-      double2 acc = vc[Ridx[k]];
-      for (int i = 0; i < s; ++i) {
-        double2 tv = B.T[i + (int64_t)k * B.ldT];
-        double2 bs = vc[Sidx[i]];
-        if (!adjoint) acc = csub(acc, cmul(tv, bs));
-        else acc = csub(acc, cmul(cconj(tv), bs));
-      }
-      t1[k] = acc;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    double2 acc = mk(0.0, 0.0);
+    if (!adjoint)
+      for (int l = 0; l < r; ++l) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], t[l]);
+    else
+      for (int l = 0; l < r; ++l) cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], t[l]);
+    double2 x = csub(vc[Ridx[k]], acc);
+    xr[k] = x;
+    vc[Ridx[k]] = x;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    double2 acc = mk(0.0, 0.0);
+    for (int k = 0; k < r; ++k) {
+      double2 tv = B.T[i + (int64_t)k * B.ldT];
+      cfma(acc, adjoint ? cconj(tv) : tv, xr[k]);
     }
-    __syncthreads();
-    // t2 = Xinv t1  (or Xinv^H t1)
-    for (int k = tid; k < r; k += blockDim.x) {
-      double2 acc = mk(0.0, 0.0);
-      for (int l = 0; l < r; ++l) {
-        if (!adjoint) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], t1[l]);
-        else cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], t1[l]);
-      }
-      t2[k] = acc;
-    }
-    __syncthreads();
-    // b_C -= X_CR t2   (or X_RC^H t2)
-    for (int i = tid; i < m; i += blockDim.x) {
-      double2 acc = mk(0.0, 0.0);
-      for (int k = 0; k < r; ++k) {
-        if (!adjoint) cfma(acc, B.XCR[i + (int64_t)k * B.ldL], t2[k]);
-        else cfma_cj(acc, B.XRC[k + (int64_t)i * B.ldU], t2[k]);
-      }
-      int dof = Cidx[i];
-      vc[dof] = csub(vc[dof], acc);
-    }
-    for (int k = tid; k < r; k += blockDim.x) vc[Ridx[k]] = t2[k];
-  } else {
-    // t1 = op(X_RC) x_C, reduction over the m columns, staged in chunks
-    for (int k = tid; k < r; k += blockDim.x) t1[k] = mk(0.0, 0.0);
-    __syncthreads();
-    const int chunk = 1024;
-    for (int j0 = 0; j0 < m; j0 += chunk) {
-      int jl = min(chunk, m - j0);
-      for (int j = tid; j < jl; j += blockDim.x) u[j] = vc[Cidx[j0 + j]];
-      __syncthreads();
-      if (!adjoint)
-        block_matvec_red<false>(B.XRC + (int64_t)j0 * B.ldU, B.ldU, r, jl, u, t2, red);
-      else
-        block_matvec_red<true>(B.XCR + j0, B.ldL, r, jl, u, t2, red);
-      for (int k = tid; k < r; k += blockDim.x) t1[k] = cadd(t1[k], t2[k]);
-      __syncthreads();
-    }
-    // x_R = b_R - op(Xinv) t1
-    for (int k = tid; k < r; k += blockDim.x) {
-      double2 acc = mk(0.0, 0.0);
-      for (int l = 0; l < r; ++l) {
-        if (!adjoint) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], t1[l]);
-        else cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], t1[l]);
-      }
-      t2[k] = csub(vc[Ridx[k]], acc);
-    }
-    __syncthreads();
-    for (int k = tid; k < r; k += blockDim.x) vc[Ridx[k]] = t2[k];
-    // x_S -= op(T) x_R
-    for (int i = tid; i < s; i += blockDim.x) {
-      double2 acc = mk(0.0, 0.0);
-      for (int k = 0; k < r; ++k) {
-        double2 tv = B.T[i + (int64_t)k * B.ldT];
-        if (!adjoint) cfma(acc, tv, t2[k]);
-        else cfma(acc, cconj(tv), t2[k]);
-      }
-      vc[Sidx[i]] = csub(vc[Sidx[i]], acc);
-    }
+    vc[Sidx[i]] = csub(vc[Sidx[i]], acc);
   }
 }
 
-void launch_sweep(const SolveBox* boxes, int b0, int nb, int rmax, double2* v, int64_t n,
-                  int nrhs, bool backward, bool adjoint, cudaStream_t st) {
-  if (nb <= 0 || rmax <= 0) return;
-  size_t sm = (size_t)(2 * rmax + 256 + 1024) * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
+static void set_smem_attr() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_fwd_z, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_fwd_c, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_bwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  done = true;
+}
+
+void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
+                  double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
+                  double2* partial, int64_t pstride, cudaStream_t st) {
+  if (sg.nb <= 0) return;
+  set_smem_attr();
+  int adj = adjoint ? 1 : 0;
+  if (!backward) {
+    size_t sm1 = (size_t)(sg.rmax + sg.smax) * sizeof(double2);
+    FMMLU_LAUNCH("sweep_fwd", st, k_fwd_z<<<dim3(sg.nb, nrhs), 256, sm1, st>>>(boxes, sg.b0, v, n, adj));
+    size_t sm2 = (size_t)sg.rmax * sizeof(double2);
+    if (sg.ni > 0)
+      FMMLU_LAUNCH("sweep_fwd_c", st, k_fwd_c<<<dim3(sg.ni, nrhs), 256, sm2, st>>>(boxes, items, sg.i0, v, n, adj));
+  } else {
+    size_t sm1 = (size_t)(kSweepChunk + 256) * sizeof(double2);
+    if (sg.ni > 0)
+      FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
+                                                                                 partial, pstride, adj));
+    size_t sm2 = (size_t)(2 * sg.rmax) * sizeof(double2);
+    FMMLU_LAUNCH("sweep_bwd", st, k_bwd_x<<<dim3(sg.nb, nrhs), 256, sm2, st>>>(boxes, sg.b0, items, v, n,
+                                                                             partial, pstride, adj));
   }
-  FMMLU_LAUNCH(backward ? "sweep_bwd" : "sweep_fwd", st,
-               k_sweep<<<dim3(nb, nrhs), 256, sm, st>>>(boxes, b0, v, n, backward ? 1 : 0,
-                                                       adjoint ? 1 : 0, rmax));
 }
 
 // ---------------------------------------------------------------------------
