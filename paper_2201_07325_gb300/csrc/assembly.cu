@@ -117,6 +117,41 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
     int i = row0 + e % rows;
     int j = e / rows;
     int jd = L.act_dof[bbase + j];
+    if (sizeof(C) == sizeof(float2)) {
+      // mixed path: complex64 kernel blocks (Schur updates rounded to fp32)
+      float2 v;
+      const float kf = (float)g.k, ef = (float)g.eta;
+      if (i < 2 * nq) {
+        const bool out = i < nq;
+        const int i2 = out ? i : i - nq;
+        const int q = qdof[i2];
+        const int t = out ? q : jd, sdof = out ? jd : q;
+        v = comb_kernel_f(g.px[t], g.py[t], g.pz[t], g.px[sdof], g.py[sdof], g.pz[sdof],
+                          (float)g.nx[sdof], (float)g.ny[sdof], (float)g.nz[sdof], kf, ef);
+        v = cscale(v, (float)(g.sw[q] * g.sw[jd]));
+        int64_t off = L.qpair[d.qpair + 2 * qloc[i2] + (out ? 0 : 1)];
+        if (off >= 0) {
+          double2 dv = out ? L.delta[off + qpos[i2] + (int64_t)j * L.cur_a0[L.qlist[d.qbeg + qloc[i2]]]]
+                           : L.delta[off + j + (int64_t)qpos[i2] * a];
+          v = cadd(v, make_float2((float)dv.x, (float)dv.y));
+        }
+      } else {
+        int l = i - 2 * nq;
+        bool incoming = l >= np;
+        if (incoming) l -= np;
+        double ux, uy, uz;
+        fib_point(l, np, ux, uy, uz);
+        double yx = d.cx + rho * ux, yy = d.cy + rho * uy, yz = d.cz + rho * uz;
+        if (!incoming)
+          v = comb_kernel_f(yx, yy, yz, g.px[jd], g.py[jd], g.pz[jd], (float)g.nx[jd],
+                            (float)g.ny[jd], (float)g.nz[jd], kf, ef);
+        else
+          v = green_f(g.px[jd], g.py[jd], g.pz[jd], yx, yy, yz, kf);
+        v = cscale(v, (float)(cg * g.sw[jd]));
+      }
+      reinterpret_cast<float2*>(M)[i + (int64_t)j * d.mmax] = v;
+      continue;
+    }
     double2 v;
     if (i < nq) {
       int q = qdof[i];
@@ -148,7 +183,7 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
       }
       v = cscale(v, s);
     }
-    M[i + (int64_t)j * d.mmax] = from_d2<C>(v);
+    reinterpret_cast<double2*>(M)[i + (int64_t)j * d.mmax] = v;
   }
 }
 

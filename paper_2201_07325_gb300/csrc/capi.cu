@@ -483,7 +483,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       std::vector<int> P(cnt);
       int tot = 0;
       for (int e = 0; e < cnt; ++e) {
-        int pmax = std::max(1, std::min(160, desc[b0 + e].mmax / 64));
+        int pmax = std::max(1, std::min(H->fp32 ? 32 : 160, desc[b0 + e].mmax / 64));
         P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * wgt[e] / wsum)));
         tot += P[e];
       }

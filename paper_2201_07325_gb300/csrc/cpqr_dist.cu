@@ -12,6 +12,8 @@
 //   3. every CTA forms the reflector from the published row and the reduced
 //      norm, updates its rows and forms partial norms of rows > j;
 //   4. CTA c reduces the partial norms of its columns.
+// With P <= kRedundantP every CTA instead reduces all partial dots and norms
+// itself (steps 2 and 4 vanish): two barriers per step instead of four.
 // Steps are separated by per-box barriers (a counter in global memory). All
 // CTAs of a launch are co-resident (cooperative launch). Every wait is
 // bounded: after kSpinLimit polls the box's abort flag is raised, the status
@@ -24,6 +26,7 @@
 namespace fmmlu {
 
 constexpr int kDistThreads = 256;
+constexpr int kRedundantP = 32;
 template <typename Rl>
 __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
                                                             const CpqrPart* __restrict__ parts,
@@ -71,16 +74,27 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
     if (lane == 0) stcg(part_norm + (int64_t)rank * a + k, acc);
   }
   BARRIER();
-  for (int k = rank + P * tid; k < a; k += P * blockDim.x) {
-    Rl s = 0;
-    for (int c = 0; c < P; ++c) s += ldcg(part_norm + (int64_t)c * a + k);
-    stcg(norm_full + k, s);
+  const bool redundant = P <= kRedundantP;
+  if (!redundant) {
+    for (int k = rank + P * tid; k < a; k += P * blockDim.x) {
+      Rl s = 0;
+      for (int c = 0; c < P; ++c) s += ldcg(part_norm + (int64_t)c * a + k);
+      stcg(norm_full + k, s);
+    }
+    BARRIER();
   }
-  BARRIER();
   if (tid == 0) s_rank = min(m, a);
   const int steps = min(m, a);
   for (int j = 0; j < steps; ++j) {
-    for (int k = j + tid; k < a; k += blockDim.x) norms[k] = ldcg(norm_full + k);
+    if (redundant) {
+      for (int k = j + tid; k < a; k += blockDim.x) {
+        Rl s = 0;
+        for (int c = 0; c < P; ++c) s += ldcg(part_norm + (int64_t)c * a + k);
+        norms[k] = s;
+      }
+    } else {
+      for (int k = j + tid; k < a; k += blockDim.x) norms[k] = ldcg(norm_full + k);
+    }
     __syncthreads();
     if (warp == 0) {
       Rl best = (Rl)-1;
@@ -130,16 +144,18 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
     if (owner)
       for (int k = j + tid; k < a; k += blockDim.x) stcg(rowj + k, M[j + k * ld]);
     BARRIER();
-    for (int k0 = j + 1; k0 < a; k0 += P * blockDim.x) {
-      // columns k = j+1 .. a-1 with (k - j - 1) % P == rank
-      int k = k0 + rank + P * tid;
-      if (k < a) {
-        C s = mk((Rl)0, (Rl)0);
-        for (int c = 0; c < P; ++c) s = cadd(s, ldcg(part_dot + (int64_t)c * a + k));
-        stcg(dot_full + k, s);
+    if (!redundant) {
+      for (int k0 = j + 1; k0 < a; k0 += P * blockDim.x) {
+        // columns k = j+1 .. a-1 with (k - j - 1) % P == rank
+        int k = k0 + rank + P * tid;
+        if (k < a) {
+          C s = mk((Rl)0, (Rl)0);
+          for (int c = 0; c < P; ++c) s = cadd(s, ldcg(part_dot + (int64_t)c * a + k));
+          stcg(dot_full + k, s);
+        }
       }
+      BARRIER();
     }
-    BARRIER();
     if (tid == 0) {
       C x0 = ldcg(rowj + j);
       Rl nx2 = norms[j];
@@ -157,7 +173,13 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
     const C v0 = s_v0;
     const Rl tau = s_tau;
     for (int k = j + 1 + tid; k < a; k += blockDim.x) {
-      C wk = ldcg(dot_full + k);
+      C wk;
+      if (redundant) {
+        wk = mk((Rl)0, (Rl)0);
+        for (int c = 0; c < P; ++c) wk = cadd(wk, ldcg(part_dot + (int64_t)c * a + k));
+      } else {
+        wk = ldcg(dot_full + k);
+      }
       cfma_cj(wk, v0, ldcg(rowj + k));
       w[k] = mk(tau * wk.x, tau * wk.y);
     }
@@ -179,15 +201,17 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
       if (tid == 0) M[j + j * ld] = s_alpha;
     }
     BARRIER();
-    for (int k0 = j + 1; k0 < a; k0 += P * blockDim.x) {
-      int k = k0 + rank + P * tid;
-      if (k < a) {
-        Rl s = 0;
-        for (int c = 0; c < P; ++c) s += ldcg(part_norm + (int64_t)c * a + k);
-        stcg(norm_full + k, s);
+    if (!redundant) {
+      for (int k0 = j + 1; k0 < a; k0 += P * blockDim.x) {
+        int k = k0 + rank + P * tid;
+        if (k < a) {
+          Rl s = 0;
+          for (int c = 0; c < P; ++c) s += ldcg(part_norm + (int64_t)c * a + k);
+          stcg(norm_full + k, s);
+        }
       }
+      BARRIER();
     }
-    BARRIER();
   }
 #undef BARRIER
   __syncthreads();

@@ -120,6 +120,35 @@ __device__ __forceinline__ double2 comb_kernel(double tx, double ty, double tz,
   return mk(d.x + eta * g.y, d.y - eta * g.x);
 }
 
+// Single-precision versions for the mixed path's ID matrix: the coordinate
+// differences are formed in fp64 (cancellation), everything after in fp32
+// with CUDA's fp32 sincos and square root.
+__device__ __forceinline__ float2 green_f(double tx, double ty, double tz, double sx, double sy,
+                                         double sz, float k) {
+  float dx = (float)(sx - tx), dy = (float)(sy - ty), dz = (float)(sz - tz);
+  float r = sqrtf(dx * dx + dy * dy + dz * dz);
+  float sn, cs;
+  sincosf(k * r, &sn, &cs);
+  float g = 1.0f / (4.0f * (float)kPi * r);
+  return make_float2(cs * g, sn * g);
+}
+
+__device__ __forceinline__ float2 comb_kernel_f(double tx, double ty, double tz, double sx,
+                                               double sy, double sz, float nx, float ny,
+                                               float nz, float k, float eta) {
+  float dx = (float)(sx - tx), dy = (float)(sy - ty), dz = (float)(sz - tz);
+  float r2 = dx * dx + dy * dy + dz * dz;
+  float r = sqrtf(r2);
+  float sn, cs;
+  sincosf(k * r, &sn, &cs);
+  float ginv = 1.0f / (4.0f * (float)kPi * r);
+  float2 g = make_float2(cs * ginv, sn * ginv);
+  float proj = (dx * nx + dy * ny + dz * nz) / r2;
+  float2 f = make_float2(-proj, k * r * proj);
+  float2 d = cmul(g, f);
+  return make_float2(d.x + eta * g.y, d.y - eta * g.x);
+}
+
 // Matrix entry A(i, j) of the scaled system without Schur updates.
 __device__ __forceinline__ double2 entry(const Geometry& g, int i, int j) {
   if (i == j) {
