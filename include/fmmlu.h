@@ -83,6 +83,11 @@ typedef struct fmmlu_opts {
                                  (reported by fmmlu_stats). Default 0.      */
   int cpqr_single;            /* 1: run every pivoted QR with one CTA per box
                                  (no row distribution). Default 0.          */
+  int schur_emulation;        /* 1 (default): Schur-complement products on the
+                                 bf16 tensor cores by an exact 7-digit
+                                 splitting of the complex128 operands (every
+                                 product exact, every rounding an fp64
+                                 addition); 0: fp64 FMA. */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if

@@ -42,6 +42,7 @@ class fmmlu_opts(ctypes.Structure):
         ("verbose", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("cpqr_single", ctypes.c_int),
+        ("schur_emulation", ctypes.c_int),
     ]
 
 

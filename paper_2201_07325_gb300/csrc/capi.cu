@@ -110,6 +110,7 @@ void default_opts(fmmlu_opts* o) {
   o->verbose = 0;
   o->profile = 0;
   o->cpqr_single = 0;
+  o->schur_emulation = 1;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -544,6 +545,23 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       gp.scratch = off;
       gj_scratch = std::max(gj_scratch, off);
     }
+    // Schur update on tensor cores: per-box slice scratch (bounds), per colour
+    std::vector<OzBoxHost> ozb(nb);
+    std::vector<int64_t> oz_seg_slices(seg_start.size(), 0), oz_seg_expo(seg_start.size(), 0);
+    int64_t oz_slices = 0, oz_expo = 0;
+    const bool use_oz = opt.schur_emulation != 0;
+    if (use_oz) {
+      for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+        int64_t so = 0, eo = 0;
+        for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e)
+          plan_oz_box(desc[e].a, desc[e].nmax, so, eo, ozb[e]);
+        oz_slices = std::max(oz_slices, so);
+        oz_expo = std::max(oz_expo, eo);
+      }
+    }
+    OzBoxHost* d_ozb = use_oz ? lw.up(ozb, st) : nullptr;
+    void* d_oz_slices = use_oz ? (void*)lw.get<uint16_t>((size_t)oz_slices) : nullptr;
+    int* d_oz_expo = use_oz ? lw.get<int>((size_t)oz_expo) : nullptr;
     CpqrPart* d_parts = lw.up(parts, st);
     unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
     unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
@@ -575,7 +593,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_xrr_inverse(LD, b0, cnt, amax, st);
       }
       launch_gemm_w(LD, b0, cnt, amax, nmaxm, st);
-      launch_schur_update(LD, b0, cnt, amax, nmaxm, st);
+      if (use_oz)
+        launch_oz_schur(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, st);
+      else
+        launch_schur_update(LD, b0, cnt, amax, nmaxm, st);
       CK(cudaGetLastError());
     }
     std::vector<BoxRun> run = ddownload(d_run, (size_t)nb, st);

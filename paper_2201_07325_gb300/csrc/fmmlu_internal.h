@@ -173,6 +173,16 @@ size_t cpqr_dist_scratch_bytes(int P, int a, bool fp32);
 int cpqr_dist_capacity(int amax, bool fp32);
 cudaError_t launch_cpqr_dist(const LevelDev& L, const CpqrPart* d_parts, int nparts,
                              unsigned char* scratch, int amax, bool fp32, cudaStream_t st);
+// ozaki.cu: Schur update on bf16 tensor cores by exact operand splitting
+struct OzBoxHost {       // per box of a colour, planned from bounds
+  int64_t a_off;         // bf16 offset of W's slices: [p][part][mpad][kp]
+  int64_t b_off;         // bf16 offset of X_RC's slices: [q][part][mpad][kp]
+  int64_t e_off;         // int offset of row exponents (mpad) then column exponents (mpad)
+  int mpad, kp;          // rows/cols padded to 64, k padded to 16
+};
+void plan_oz_box(int a, int nmax, int64_t& slice_off, int64_t& expo_off, OzBoxHost& out);
+void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
+                     int* expo, int amax, int nmax_max, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);

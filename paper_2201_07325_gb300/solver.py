@@ -29,7 +29,8 @@ class Factorization:
 
     def __init__(self, points, normals, weights, k: float, eps: float, eta: float | None = None,
                  leaf_size: int = 64, n_proxy: int = 300, proxy_radius_factor: float = 1.5,
-                 precision: int = B.PRECISION_AUTO, verbose: int = 0, device=None):
+                 precision: int = B.PRECISION_AUTO, verbose: int = 0, device=None,
+                 **extra_opts):
         device = torch.device(device or "cuda")
         self.device = device
         self.points = _as_cuda(points, torch.float64, device)
@@ -42,7 +43,7 @@ class Factorization:
         self.opts = B.fmmlu_default_opts(
             leaf_size=leaf_size, eta=self.eta if eta is not None else math.nan,
             n_proxy=n_proxy, proxy_radius_factor=proxy_radius_factor, precision=precision,
-            verbose=verbose)
+            verbose=verbose, **extra_opts)
         self.tree = None
         self.handle = None
         self.tree = B.fmmlu_build_tree(self.points, self.opts)

@@ -151,6 +151,27 @@ def test_eps_to_zero_is_dense_lu(pkg, ell):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
 
 
+@pytest.mark.parametrize("emul", [0, 1])
+def test_schur_emulation_exact_limit_and_accuracy(pkg, ell, emul):
+    """Schur products in fp64 FMA (0) or on bf16 tensor cores by exact operand
+    splitting (1): eps -> 0 must still be the dense LU, eps = 1e-6 within 10 eps,
+    and both modes must agree far below eps."""
+    s, A, b, xd = ell
+    fac = _gpu_factor(pkg, s, K, 1e-14, leaf_size=24, precision=pkg.PRECISION_FP64,
+                      schur_emulation=emul)
+    x = fac.solve(torch.from_numpy(b)).cpu().numpy()
+    fac.free()
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
+    xs = {}
+    for mode in (0, 1):
+        fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          schur_emulation=mode)
+        xs[mode] = fac.solve(torch.from_numpy(b)).cpu().numpy()
+        fac.free()
+    assert np.linalg.norm(A @ xs[emul] - b) / np.linalg.norm(b) <= 1e-5
+    assert np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[0]) <= 1e-7
+
+
 def test_single_box_is_dense_lu(pkg):
     s = synth.ellipsoid_uniform(50, seed=3)
     A = kernel.dense_matrix(s.points, s.normals, s.weights, 3.0, 3.0)
