@@ -27,6 +27,14 @@ namespace fmmlu {
 
 constexpr int kDistThreads = 256;
 constexpr int kRedundantP = 32;
+// sum over the 8 lanes of a segment (lanes 8c .. 8c+7)
+template <typename T> __device__ __forceinline__ T seg8_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 template <typename Rl>
 __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
                                                             const CpqrPart* __restrict__ parts,
@@ -66,12 +74,16 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
     if (!box_barrier(ctr, nbar * (unsigned)P, abort_flag, L.status)) return;       \
   } while (0)
 
+  // column work: each warp takes 4 columns at a time, 8 lanes per column
+  const int sub = lane >> 3, sl = lane & 7;
   for (int k = tid; k < a; k += blockDim.x) perm[k] = k;
-  for (int k = warp; k < a; k += nw) {
+  for (int kk = 4 * warp; kk < a; kk += 4 * nw) {
+    const int k = kk + sub;
     Rl acc = 0;
-    for (int i = r0 + lane; i < r1; i += 32) cnorm_acc(acc, M[i + k * ld]);
-    acc = warp_sum(acc);
-    if (lane == 0) stcg(part_norm + (int64_t)rank * a + k, acc);
+    if (k < a)
+      for (int i = r0 + sl; i < r1; i += 8) cnorm_acc(acc, M[i + k * ld]);
+    acc = seg8_sum(acc);
+    if (sl == 0 && k < a) stcg(part_norm + (int64_t)rank * a + k, acc);
   }
   BARRIER();
   const bool redundant = P <= kRedundantP;
@@ -133,12 +145,14 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
     }
     __syncthreads();
     const int lo = max(r0, j + 1);
-    for (int k = j + 1 + warp; k < a; k += nw) {
+    for (int kk = j + 1 + 4 * warp; kk < a; kk += 4 * nw) {
+      const int k = kk + sub;
       C acc = mk((Rl)0, (Rl)0);
-      for (int i = lo + lane; i < r1; i += 32) cfma_cj(acc, M[i + j * ld], M[i + k * ld]);
-      acc.x = warp_sum(acc.x);
-      acc.y = warp_sum(acc.y);
-      if (lane == 0) stcg(part_dot + (int64_t)rank * a + k, acc);
+      if (k < a)
+        for (int i = lo + sl; i < r1; i += 8) cfma_cj(acc, M[i + j * ld], M[i + k * ld]);
+      acc.x = seg8_sum(acc.x);
+      acc.y = seg8_sum(acc.y);
+      if (sl == 0 && k < a) stcg(part_dot + (int64_t)rank * a + k, acc);
     }
     const bool owner = r0 <= j && j < r1;
     if (owner)
@@ -184,17 +198,20 @@ __global__ void __launch_bounds__(kDistThreads) k_cpqr_dist(LevelDev L,
       w[k] = mk(tau * wk.x, tau * wk.y);
     }
     __syncthreads();
-    for (int k = j + 1 + warp; k < a; k += nw) {
-      const C tw = w[k];
+    for (int kk = j + 1 + 4 * warp; kk < a; kk += 4 * nw) {
+      const int k = kk + sub;
       Rl acc = 0;
-      for (int i = lo + lane; i < r1; i += 32) {
-        C t = M[i + k * ld];
-        cfms(t, M[i + j * ld], tw);
-        M[i + k * ld] = t;
-        cnorm_acc(acc, t);
+      if (k < a) {
+        const C tw = w[k];
+        for (int i = lo + sl; i < r1; i += 8) {
+          C t = M[i + k * ld];
+          cfms(t, M[i + j * ld], tw);
+          M[i + k * ld] = t;
+          cnorm_acc(acc, t);
+        }
       }
-      acc = warp_sum(acc);
-      if (lane == 0) stcg(part_norm + (int64_t)rank * a + k, acc);
+      acc = seg8_sum(acc);
+      if (sl == 0 && k < a) stcg(part_norm + (int64_t)rank * a + k, acc);
     }
     if (owner) {
       for (int k = j + 1 + tid; k < a; k += blockDim.x) M[j + k * ld] = csub(M[j + k * ld], cmul(v0, w[k]));
