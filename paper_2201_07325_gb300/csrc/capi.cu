@@ -583,8 +583,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
       }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
-      launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st);
-      launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st);
+      const int kskip = use_oz ? kOzInnerMin : 0;
+      launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
+      launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
+      if (use_oz) {
+        launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 0, st);
+        launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 1, st);
+      }
       launch_gemm_xrr(LD, b0, cnt, amax, st);
       if (gplan[sgi].dist) {
         CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
@@ -592,11 +597,12 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       } else {
         launch_xrr_inverse(LD, b0, cnt, amax, st);
       }
-      launch_gemm_w(LD, b0, cnt, amax, nmaxm, st);
+      launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
+      if (use_oz)
+        launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 2, st);
+      launch_schur_update(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_oz)
         launch_oz_schur(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, st);
-      else
-        launch_schur_update(LD, b0, cnt, amax, nmaxm, st);
       CK(cudaGetLastError());
     }
     std::vector<BoxRun> run = ddownload(d_run, (size_t)nb, st);

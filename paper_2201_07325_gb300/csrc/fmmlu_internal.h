@@ -183,21 +183,26 @@ struct OzBoxHost {       // per box of a colour, planned from bounds
 void plan_oz_box(int a, int nmax, int64_t& slice_off, int64_t& expo_off, OzBoxHost& out);
 void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
                      int* expo, int amax, int nmax_max, cudaStream_t st);
+// which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}
+void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
+                          int* expo, int amax, int nmax_max, int which, cudaStream_t st);
+constexpr int kOzInnerMin = 32;   // inner dimension from which the tensor-core path is used
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);
 cudaError_t launch_gj_dist(const LevelDev& L, const CpqrPart* d_parts, int nparts,
                            unsigned char* scratch, int amax, cudaStream_t st);
+// kskip > 0: leave boxes whose inner dimension is >= kskip to the tensor-core path
 void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                    cudaStream_t st);
+                    cudaStream_t st, int kskip = 0);
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                    cudaStream_t st);
+                    cudaStream_t st, int kskip = 0);
 void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
 void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                   cudaStream_t st);
+                   cudaStream_t st, int kskip = 0);
 void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                         cudaStream_t st);
+                         cudaStream_t st, int kskip = 0);
 void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
                         cudaStream_t st);
 // solve.cu

@@ -280,12 +280,12 @@ __device__ __forceinline__ bool tile_of(int m, int n, int& tm, int& tn) {
 }
 
 // G1[s:a, :] -= T^T G1[0:s, :]     (r x (a+n), k = s)
-__global__ void __launch_bounds__(256) k_gemm_g1(LevelDev L, int b0) {
+__global__ void __launch_bounds__(256) k_gemm_g1(LevelDev L, int b0, int kskip) {
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int a = d.a, s = run.s, r = run.r, n = run.n;
-  if (r == 0 || s == 0) return;
+  if (r == 0 || s == 0 || (kskip > 0 && s >= kskip)) return;
   int tm, tn;
   if (!tile_of(r, a + n, tm, tn)) return;
   double2* G1 = L.arena + d.G1_off;
@@ -295,12 +295,12 @@ __global__ void __launch_bounds__(256) k_gemm_g1(LevelDev L, int b0) {
 }
 
 // G3[:, s:a] -= G3[:, 0:s] T       ((a+n) x r, k = s)
-__global__ void __launch_bounds__(256) k_gemm_g3(LevelDev L, int b0) {
+__global__ void __launch_bounds__(256) k_gemm_g3(LevelDev L, int b0, int kskip) {
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int a = d.a, s = run.s, r = run.r, n = run.n;
-  if (r == 0 || s == 0) return;
+  if (r == 0 || s == 0 || (kskip > 0 && s >= kskip)) return;
   int tm, tn;
   if (!tile_of(a + n, r, tm, tn)) return;
   int64_t ld3 = a + d.nmax;
@@ -311,12 +311,12 @@ __global__ void __launch_bounds__(256) k_gemm_g3(LevelDev L, int b0) {
 }
 
 // W = X_CR Xinv       ((s+n) x r, k = r)
-__global__ void __launch_bounds__(256) k_gemm_w(LevelDev L, int b0) {
+__global__ void __launch_bounds__(256) k_gemm_w(LevelDev L, int b0, int kskip) {
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int a = d.a, s = run.s, r = run.r, n = run.n;
-  if (r == 0) return;
+  if (r == 0 || (kskip > 0 && r >= kskip)) return;
   int tm, tn;
   if (!tile_of(s + n, r, tm, tn)) return;
   int64_t ld3 = a + d.nmax;
@@ -343,13 +343,13 @@ struct EpiSchur {
   }
 };
 
-__global__ void __launch_bounds__(256) k_schur(LevelDev L, int b0) {
+__global__ void __launch_bounds__(256) k_schur(LevelDev L, int b0, int kskip) {
   __shared__ int rloc[kTile], rpos[kTile], cloc[kTile], cpos[kTile];
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int a = d.a, s = run.s, r = run.r, n = run.n;
-  if (r == 0) return;
+  if (r == 0 || (kskip > 0 && r >= kskip)) return;
   int tm, tn;
   if (!tile_of(s + n, s + n, tm, tn)) return;
   const int* perm = L.iarena + d.idx_off + a + d.nmax;
@@ -378,30 +378,31 @@ static inline unsigned tiles(int m, int n) {
 }
 
 void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                    cudaStream_t st) {
+                    cudaStream_t st, int kskip) {
   if (nb <= 0) return;
   FMMLU_LAUNCH("gemm_g1", st,
-               k_gemm_g1<<<dim3(tiles(amax, 2 * amax + nmax_max), nb), 256, 0, st>>>(L, b0));
+               k_gemm_g1<<<dim3(tiles(amax, 2 * amax + nmax_max), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                    cudaStream_t st) {
+                    cudaStream_t st, int kskip) {
   if (nb <= 0) return;
   FMMLU_LAUNCH("gemm_g3", st,
-               k_gemm_g3<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0));
+               k_gemm_g3<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
-void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max, cudaStream_t st) {
+void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max, cudaStream_t st,
+                   int kskip) {
   if (nb <= 0) return;
   FMMLU_LAUNCH("gemm_w", st,
-               k_gemm_w<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0));
+               k_gemm_w<<<dim3(tiles(amax + nmax_max, amax), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
 void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
-                         cudaStream_t st) {
+                         cudaStream_t st, int kskip) {
   if (nb <= 0) return;
   FMMLU_LAUNCH("schur_update", st,
-               k_schur<<<dim3(tiles(amax + nmax_max, amax + nmax_max), nb), 256, 0, st>>>(L, b0));
+               k_schur<<<dim3(tiles(amax + nmax_max, amax + nmax_max), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
 // ---------------------------------------------------------------------------

@@ -18,11 +18,14 @@
 // exact and every rounding is an fp64 addition.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace fmmlu {
 
 constexpr int kOzSlices = 7;
+constexpr int kOzMinK = kOzInnerMin;   // smaller inner dimensions use the fp64 FMA kernels
 
 using OzBox = OzBoxHost;
 
@@ -32,13 +35,20 @@ __device__ __forceinline__ int row_exponent(double m) {
   return e;
 }
 
-__device__ __forceinline__ void split_digits(double x, __nv_bfloat16* out, int64_t stride) {
-  // x in (-1, 1): base-256 digits, each an integer in [-255, 255]
+// v * 2^-e in (-1, 1): its first seven signed base-256 digits (each an integer
+// in [-255, 255], exact in bf16). The scaled value times 2^56 is truncated to a
+// 56-bit integer U (one exact scaling and one conversion); digit p is byte
+// 6 - p of |U| with the sign of v -- the same digits as repeatedly scaling by
+// 256 and truncating.
+__device__ __forceinline__ void split_digits(double v, int e, __nv_bfloat16* out,
+                                             int64_t stride) {
+  const long long F = (long long)ldexp(v, 56 - e);   // |F| < 2^56, truncated toward 0
+  const bool neg = F < 0;
+  const unsigned long long U = (unsigned long long)(neg ? -F : F);
+#pragma unroll
   for (int p = 0; p < kOzSlices; ++p) {
-    x *= 256.0;
-    double d = trunc(x);
-    x -= d;
-    out[p * stride] = __double2bfloat16(d);
+    int dgt = (int)((U >> (8 * (kOzSlices - 1 - p))) & 255ull);
+    out[p * stride] = __int2bfloat16_rn(neg ? -dgt : dgt);
   }
 }
 
@@ -49,7 +59,7 @@ __global__ void __launch_bounds__(256) k_oz_split(LevelDev L, int b0, const OzBo
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   const int s = run.s, r = run.r, n = run.n;
-  if (r == 0) return;
+  if (r < kOzMinK) return;
   const OzBox o = oz[blockIdx.z];
   const int m = s + n;
   const int mt = (m + 63) & ~63;
@@ -81,8 +91,8 @@ __global__ void __launch_bounds__(256) k_oz_split(LevelDev L, int b0, const OzBo
       double2 v = make_double2(0.0, 0.0);
       if (i < m && k < r) v = cols ? X[k + (int64_t)i * d.a] : W[i + (int64_t)k * lw];
       __nv_bfloat16* dst = base + (int64_t)i * o.kp + k;
-      split_digits(ldexp(v.x, -e), dst, pstride);
-      split_digits(ldexp(v.y, -e), dst + partstride, pstride);
+      split_digits(v.x, e, dst, pstride);
+      split_digits(v.y, e, dst + partstride, pstride);
     }
   }
 }
@@ -130,53 +140,24 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) {
                : "r"(a));
 }
 
-// one CTA per 64 x 64 tile of the box's (s+n) x (s+n) Schur update
-__global__ void __launch_bounds__(256) k_oz_schur(LevelDev L, int b0, const OzBox* __restrict__ oz,
-                                                  const __nv_bfloat16* __restrict__ slices,
-                                                  const int* __restrict__ expo) {
-  extern __shared__ __align__(16) __nv_bfloat16 sm[];
-  __shared__ int rloc[64], rpos[64], cloc[64], cpos[64], rex[64], cex[64];
-  const int b = b0 + blockIdx.y;
-  const BoxDesc d = L.desc[b];
-  const BoxRun run = L.run[b];
-  const int s = run.s, r = run.r, n = run.n;
-  if (r == 0) return;
-  const OzBox o = oz[blockIdx.y];
-  const int m = s + n;
-  const int tms = (m + 63) / 64;
-  if ((int)blockIdx.x >= tms * tms) return;
-  const int tm = blockIdx.x % tms, tn = blockIdx.x / tms;
-  const int i0 = tm * 64, j0 = tn * 64;
-  const int kt = (r + 15) & ~15;
-  const int* perm = L.iarena + d.idx_off + d.a + d.nmax;
-  const int* ndof = L.rows + d.rows_off + 3 * d.qmax;
-  const int* npos = ndof + d.nmax;
-  const int* nloc = npos + d.nmax;
-  const int* ex = expo + o.e_off;
-  if (threadIdx.x < 64) {
-    int t = threadIdx.x;
-    int i = i0 + t, j = j0 + t;
-    if (i < s) { rloc[t] = 0; rpos[t] = perm[i]; }
-    else if (i < m) { rloc[t] = nloc[i - s]; rpos[t] = npos[i - s]; }
-    if (j < s) { cloc[t] = 0; cpos[t] = perm[j]; }
-    else if (j < m) { cloc[t] = nloc[j - s]; cpos[t] = npos[j - s]; }
-    rex[t] = i < m ? ex[i] : 0;
-    cex[t] = j < m ? ex[o.mpad + j] : 0;
-  }
+// The digit-pair products of one 64 x 64 output tile: for every scale
+// d = p + q, stage A_p and B_q blocks (cp.async, double-buffered), multiply on
+// the tensor cores (exact fp32 block sums), add the pairs of equal scale as
+// int32 and accumulate each scale once in fp64. acc receives the tile of
+// sum_{p+q<=6} 2^{-8(p+q+2)} (A_p B_q) (before the row/column exponents).
+__device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv_bfloat16* Asl,
+                                                   const __nv_bfloat16* Bsl, int64_t partstride,
+                                                   int kp, int i0, int j0, int kt,
+                                                   double (&acc)[4][4][2]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tq = lane & 3;
   const int wr = (warp & 3) * 16;
   const int wc = (warp >> 2) * 32;
-  const int64_t partstride = (int64_t)o.mpad * o.kp;
   const int64_t pstride = 2 * partstride;
-  const __nv_bfloat16* Asl = slices + o.a_off;
-  const __nv_bfloat16* Bsl = slices + o.b_off;
   // ldmatrix row addresses (element offsets inside a staged part)
   const int mi = lane >> 3, ri = lane & 7;
   const int a_off = (wr + ri + (mi & 1) * 8) * kOzLd + (mi >> 1) * 8;
   // B: matrices (n 0-7,k 0-7), (n 0-7,k 8-15), (n 8-15,k 0-7), (n 8-15,k 8-15)
   const int b_off = (wc + ri + (mi >> 1) * 8) * kOzLd + (mi & 1) * 8;
-  double acc[4][4][2];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -186,8 +167,8 @@ __global__ void __launch_bounds__(256) k_oz_schur(LevelDev L, int b0, const OzBo
   auto stage = [&](int d, int kb_i, int p, int buf) {
     const int kb = kb_i * kOzKB, klen = min(kOzKB, kt - kb);
     __nv_bfloat16* dA = sm + buf * 2 * kOzStage;
-    stage_block(dA, Asl + p * pstride, partstride, o.kp, i0, kb, klen);
-    stage_block(dA + kOzStage, Bsl + (d - p) * pstride, partstride, o.kp, j0, kb, klen);
+    stage_block(dA, Asl + p * pstride, partstride, kp, i0, kb, klen);
+    stage_block(dA + kOzStage, Bsl + (d - p) * pstride, partstride, kp, j0, kb, klen);
     cp_async_commit();
   };
   int buf = 0;
@@ -268,6 +249,48 @@ __global__ void __launch_bounds__(256) k_oz_schur(LevelDev L, int b0, const OzBo
         acc[u][e][1] = fma((double)G[u][e][1], scale, acc[u][e][1]);
       }
   }
+}
+
+// one CTA per 64 x 64 tile of the box's (s+n) x (s+n) Schur update
+__global__ void __launch_bounds__(256) k_oz_schur(LevelDev L, int b0, const OzBox* __restrict__ oz,
+                                                  const __nv_bfloat16* __restrict__ slices,
+                                                  const int* __restrict__ expo) {
+  extern __shared__ __align__(16) __nv_bfloat16 sm[];
+  __shared__ int rloc[64], rpos[64], cloc[64], cpos[64], rex[64], cex[64];
+  const int b = b0 + blockIdx.y;
+  const BoxDesc d = L.desc[b];
+  const BoxRun run = L.run[b];
+  const int s = run.s, r = run.r, n = run.n;
+  if (r < kOzMinK) return;   // small inner dimension: fp64 FMA kernel
+  const OzBox o = oz[blockIdx.y];
+  const int m = s + n;
+  const int tms = (m + 63) / 64;
+  if ((int)blockIdx.x >= tms * tms) return;
+  const int tm = blockIdx.x % tms, tn = blockIdx.x / tms;
+  const int i0 = tm * 64, j0 = tn * 64;
+  const int kt = (r + 15) & ~15;
+  const int* perm = L.iarena + d.idx_off + d.a + d.nmax;
+  const int* ndof = L.rows + d.rows_off + 3 * d.qmax;
+  const int* npos = ndof + d.nmax;
+  const int* nloc = npos + d.nmax;
+  const int* ex = expo + o.e_off;
+  if (threadIdx.x < 64) {
+    int t = threadIdx.x;
+    int i = i0 + t, j = j0 + t;
+    if (i < s) { rloc[t] = 0; rpos[t] = perm[i]; }
+    else if (i < m) { rloc[t] = nloc[i - s]; rpos[t] = npos[i - s]; }
+    if (j < s) { cloc[t] = 0; cpos[t] = perm[j]; }
+    else if (j < m) { cloc[t] = nloc[j - s]; cpos[t] = npos[j - s]; }
+    rex[t] = i < m ? ex[i] : 0;
+    cex[t] = j < m ? ex[o.mpad + j] : 0;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wr = (warp & 3) * 16;
+  const int wc = (warp >> 2) * 32;
+  double acc[4][4][2];
+  oz_tile_accumulate(sm, slices + o.a_off, slices + o.b_off, (int64_t)o.mpad * o.kp, o.kp, i0, j0,
+                     kt, acc);
   __syncthreads();
   // epilogue: scale by 2^(E_i + F_j) in fp64 and subtract from Delta
   const int cnt = 1 + d.ncnt;
@@ -290,6 +313,174 @@ __global__ void __launch_bounds__(256) k_oz_schur(LevelDev L, int b0, const OzBo
       double2 cur = *pz;
       *pz = make_double2(cur.x - vr, cur.y - vi);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Generic exactly-split complex GEMM C <- epi(op(A) op(B)) for the other
+// fp64 products of the elimination (same splitting and exact accumulation as
+// the Schur update above). A problem supplies the sizes of one box, element
+// accessors of op(A) (m x k) and op(B) (k x n), and the epilogue.
+// Boxes whose inner dimension is below kOzMinK use the fp64 FMA kernels.
+
+struct ProbW {      // W = X_CR X_RR^{-1}: (s+n) x r x r, stored
+  __device__ static bool dims(const BoxDesc& d, const BoxRun& rr, int& m, int& n, int& k) {
+    m = rr.s + rr.n; n = rr.r; k = rr.r; return rr.r >= kOzMinK;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int kk) {
+    return L.arena[d.G3_off + i + (int64_t)(rr.s + kk) * (d.a + d.nmax)];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.Xinv_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int j,
+                             double vr, double vi) {
+    L.Wbuf[d.W_off + i + (int64_t)j * (d.a + d.nmax)] = make_double2(vr, vi);
+  }
+};
+
+struct ProbG1 {     // G1[s:a, :] -= T^T G1[0:s, :]: r x (a+n) x s
+  __device__ static bool dims(const BoxDesc& d, const BoxRun& rr, int& m, int& n, int& k) {
+    m = rr.r; n = d.a + rr.n; k = rr.s; return rr.r > 0 && rr.s >= kOzMinK;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.arena[d.T_off + kk + (int64_t)i * d.a];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.G1_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int j,
+                             double vr, double vi) {
+    double2* c = L.arena + d.G1_off + (rr.s + i) + (int64_t)j * d.a;
+    double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
+};
+
+struct ProbG3 {     // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
+  __device__ static bool dims(const BoxDesc& d, const BoxRun& rr, int& m, int& n, int& k) {
+    m = d.a + rr.n; n = rr.r; k = rr.s; return rr.r > 0 && rr.s >= kOzMinK;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.arena[d.G3_off + i + (int64_t)kk * (d.a + d.nmax)];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.T_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int j,
+                             double vr, double vi) {
+    double2* c = L.arena + d.G3_off + i + (int64_t)(rr.s + j) * (d.a + d.nmax);
+    double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
+};
+
+// rows of op(A) (y = 0) or columns of op(B) (y = 1) into digit slices
+template <class Prob>
+__global__ void __launch_bounds__(256) k_ozg_split(LevelDev L, int b0, const OzBox* __restrict__ oz,
+                                                   __nv_bfloat16* slices, int* expo) {
+  const int b = b0 + blockIdx.z;
+  const BoxDesc d = L.desc[b];
+  const BoxRun rr = L.run[b];
+  int m, n, k;
+  if (!Prob::dims(d, rr, m, n, k)) return;
+  const OzBox o = oz[blockIdx.z];
+  const bool cols = blockIdx.y == 1;
+  const int len = cols ? n : m;
+  const int lt = (len + 63) & ~63;
+  const int kt = (k + 15) & ~15;
+  const int i0 = blockIdx.x * 32;
+  if (i0 >= lt) return;
+  __nv_bfloat16* base = slices + (cols ? o.b_off : o.a_off);
+  int* ex = expo + o.e_off + (cols ? o.mpad : 0);
+  const int64_t partstride = (int64_t)o.mpad * o.kp;
+  const int64_t pstride = 2 * partstride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rr2 = warp; rr2 < 32; rr2 += 8) {
+    const int i = i0 + rr2;
+    if (i >= lt) break;
+    double mx = 0.0;
+    if (i < len)
+      for (int kk = lane; kk < k; kk += 32) {
+        double2 v = cols ? Prob::B(L, d, rr, kk, i) : Prob::A(L, d, rr, i, kk);
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+    const int e = row_exponent(mx);
+    if (lane == 0) ex[i] = e;
+    for (int kk = lane; kk < kt; kk += 32) {
+      double2 v = make_double2(0.0, 0.0);
+      if (i < len && kk < k) v = cols ? Prob::B(L, d, rr, kk, i) : Prob::A(L, d, rr, i, kk);
+      __nv_bfloat16* dst = base + (int64_t)i * o.kp + kk;
+      split_digits(v.x, e, dst, pstride);
+      split_digits(v.y, e, dst + partstride, pstride);
+    }
+  }
+}
+
+template <class Prob>
+__global__ void __launch_bounds__(256) k_ozg_gemm(LevelDev L, int b0, const OzBox* __restrict__ oz,
+                                                  const __nv_bfloat16* __restrict__ slices,
+                                                  const int* __restrict__ expo) {
+  extern __shared__ __align__(16) __nv_bfloat16 sm[];
+  __shared__ int rex[64], cex[64];
+  const int b = b0 + blockIdx.y;
+  const BoxDesc d = L.desc[b];
+  const BoxRun rr = L.run[b];
+  int m, n, k;
+  if (!Prob::dims(d, rr, m, n, k)) return;
+  const OzBox o = oz[blockIdx.y];
+  const int tms = (m + 63) / 64, tns = (n + 63) / 64;
+  if ((int)blockIdx.x >= tms * tns) return;
+  const int i0 = (blockIdx.x % tms) * 64, j0 = (blockIdx.x / tms) * 64;
+  const int kt = (k + 15) & ~15;
+  const int* ex = expo + o.e_off;
+  if (threadIdx.x < 64) {
+    int t = threadIdx.x;
+    rex[t] = i0 + t < m ? ex[i0 + t] : 0;
+    cex[t] = j0 + t < n ? ex[o.mpad + j0 + t] : 0;
+  }
+  double acc[4][4][2];
+  oz_tile_accumulate(sm, slices + o.a_off, slices + o.b_off, (int64_t)o.mpad * o.kp, o.kp, i0, j0,
+                     kt, acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wr = (warp & 3) * 16, wc = (warp >> 2) * 32;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int li = wr + g + ((e >> 1) ? 8 : 0);
+      const int lj = wc + 8 * u + 2 * tq + (e & 1);
+      const int i = i0 + li, j = j0 + lj;
+      if (i >= m || j >= n) continue;
+      const int sc = rex[li] + cex[lj];
+      Prob::epi(L, d, rr, i, j, ldexp(acc[u][e][0], sc), ldexp(acc[u][e][1], sc));
+    }
+}
+
+template <class Prob>
+static void launch_ozg(const char* name, const LevelDev& L, int b0, int nb, const OzBox* oz,
+                       __nv_bfloat16* sl, int* expo, int mmax, int nmax, cudaStream_t st) {
+  const size_t smem = (size_t)4 * kOzStage * sizeof(__nv_bfloat16);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ozg_gemm<Prob>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  int big = std::max(mmax, nmax);
+  dim3 gs((unsigned)((big + 63) / 64 * 2), 2, nb);
+  FMMLU_LAUNCH("oz_split", st, k_ozg_split<Prob><<<gs, 256, 0, st>>>(L, b0, oz, sl, expo));
+  dim3 gm((unsigned)(((mmax + 63) / 64) * ((nmax + 63) / 64)), nb);
+  FMMLU_LAUNCH(name, st, k_ozg_gemm<Prob><<<gm, 256, smem, st>>>(L, b0, oz, sl, expo));
+}
+
+void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
+                          int* expo, int amax, int nmax_max, int which, cudaStream_t st) {
+  if (nb <= 0) return;
+  __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(slices);
+  if (which == 0) launch_ozg<ProbG1>("gemm_g1", L, b0, nb, d_oz, sl, expo, amax, amax + nmax_max, st);
+  if (which == 1) launch_ozg<ProbG3>("gemm_g3", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
+  if (which == 2) launch_ozg<ProbW>("gemm_w", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
 }
 
 size_t oz_slice_elems(int a, int nmax) {
