@@ -54,6 +54,14 @@ extern "C" {
 #define FMMLU_ERR_TIMEOUT -7      /* a bounded device wait gave up           */
 #define FMMLU_ERR_LIMIT -8        /* a size exceeds a documented maximum     */
 
+#define FMMLU_ID_AUTO 0           /* Gram form when eps_ID >= 1e-7, else QR */
+#define FMMLU_ID_HOUSEHOLDER 1    /* column-pivoted Householder QR of the ID
+                                     matrix M                               */
+#define FMMLU_ID_GRAM 2           /* pivoted Cholesky of G = M^H M, with G
+                                     formed exactly on the tensor cores; its
+                                     fp64 rounding is ~1e-16 |G|, so the
+                                     rank rule resolves eps_ID down to about
+                                     1e-7 (AUTO uses QR below that)         */
 #define FMMLU_PRECISION_AUTO 0    /* mixed when eps >= 1e-5, else fp64       */
 #define FMMLU_PRECISION_FP64 1    /* everything complex128                   */
 #define FMMLU_PRECISION_MIXED 2   /* ID matrix assembly and pivoted QR in
@@ -88,6 +96,9 @@ typedef struct fmmlu_opts {
                                  splitting of the complex128 operands (every
                                  product exact, every rounding an fp64
                                  addition); 0: fp64 FMA. */
+  int id_method;              /* FMMLU_ID_*: how the ID of Def. ID picks its
+                                 skeleton (the same greedy column selection
+                                 either way). Default FMMLU_ID_AUTO.        */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if

@@ -23,6 +23,7 @@ ERRORS = {
     -5: "NONFINITE", -6: "DEPTH_CAP", -7: "TIMEOUT", -8: "LIMIT",
 }
 PRECISION_AUTO, PRECISION_FP64, PRECISION_MIXED = 0, 1, 2
+ID_AUTO, ID_HOUSEHOLDER, ID_GRAM = 0, 1, 2
 
 
 class FmmluError(RuntimeError):
@@ -43,6 +44,7 @@ class fmmlu_opts(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("cpqr_single", ctypes.c_int),
         ("schur_emulation", ctypes.c_int),
+        ("id_method", ctypes.c_int),
     ]
 
 
@@ -274,7 +276,7 @@ __all__ = [
     "fmmlu_factor", "fmmlu_solve", "fmmlu_solve_adjoint", "fmmlu_matvec", "fmmlu_stats",
     "fmmlu_tree_describe", "fmmlu_free", "fmmlu_last_error", "parse_tree_description",
     "fmmlu_kernel_launches", "fmmlu_profile_reset", "fmmlu_solve_noalloc",
-    "PRECISION_AUTO", "PRECISION_FP64", "PRECISION_MIXED",
+    "PRECISION_AUTO", "PRECISION_FP64", "PRECISION_MIXED", "ID_AUTO", "ID_HOUSEHOLDER", "ID_GRAM",
 ]
 
 _ = math  # (kept for users composing eta = nan)

@@ -111,6 +111,7 @@ void default_opts(fmmlu_opts* o) {
   o->profile = 0;
   o->cpqr_single = 0;
   o->schur_emulation = 1;
+  o->id_method = FMMLU_ID_AUTO;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -123,6 +124,7 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (o.n_proxy < 8 || o.n_proxy > 100000) throw Error(FMMLU_ERR_INVALID_ARG, "n_proxy out of [8, 100000]");
   if (o.precision < 0 || o.precision > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad precision");
   if (!(o.eps_id_divisor > 0.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps_id_divisor must be > 0");
+  if (o.id_method < 0 || o.id_method > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad id_method");
   return o;
 }
 
@@ -141,6 +143,7 @@ struct fmmlu_handle {
   int64_t n = 0;
   double k = 0, eta = 0, eps = 0;
   bool fp32 = false;
+  bool gram = false;           // ID by pivoted Cholesky of M^H M
   DevPool mem;                 // factors, plans, permutation
   int* d_perm = nullptr;
   SolveBox* d_boxes = nullptr;
@@ -316,6 +319,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   H->fp32 = opt.precision == FMMLU_PRECISION_MIXED ||
             (opt.precision == FMMLU_PRECISION_AUTO && eps >= 1e-5);
   const double eps_id = eps / opt.eps_id_divisor;
+  // Gram form of the ID: fp64 rounding of G = M^H M is ~1e-16 |G|, far below
+  // the eps_ID^2 |G| the rank rule must resolve while eps_ID >= 1e-7
+  const bool use_gram = opt.id_method == FMMLU_ID_GRAM ||
+                        (opt.id_method == FMMLU_ID_AUTO && eps_id >= 1e-7);
+  H->gram = use_gram;
   H->profile = opt.profile != 0;
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
   Timer total_timer;
@@ -332,7 +340,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
 
   std::ostringstream js;
   js << "{\"n\": " << n << ", \"k\": " << k << ", \"eta\": " << H->eta << ", \"eps\": " << eps
-     << ", \"precision\": \"" << (H->fp32 ? "mixed" : "fp64") << "\", \"nlevels\": " << T.nlevels
+     << ", \"precision\": \"" << (H->fp32 ? "mixed" : "fp64") << "\", \"id_method\": \"" << (H->gram ? "gram" : "householder") << "\", \"nlevels\": " << T.nlevels
      << ", \"levels\": [";
   std::vector<SolveBox> plan;
   std::vector<SweepItem> items;
@@ -464,6 +472,19 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     // CPQR plan per colour: boxes share the co-resident CTAs in proportion to
     // their work (rows x a^2); colours with many boxes use one CTA per box.
     struct ColPlan { int pbeg = 0, np = 0; int64_t scratch = 0; bool dist = false; };
+    // colours whose largest box exceeds the pivoted Cholesky's shared memory
+    // take the Householder QR
+    std::vector<char> gram_col(seg_start.size(), 0);
+    if (use_gram) {
+      int dev = 0, optin = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+        int amax = 1;
+        for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) amax = std::max(amax, desc[e].a);
+        gram_col[sgi] = pchol_smem(amax) <= (size_t)optin ? 1 : 0;
+      }
+    }
     std::vector<ColPlan> cplan(seg_start.size());
     std::vector<CpqrPart> parts;
     int64_t cpqr_scratch = 0;
@@ -473,7 +494,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       for (int e = b0; e < b0 + cnt; ++e) amax = std::max(amax, desc[e].a);
       int cap = cpqr_dist_capacity(amax, H->fp32);
       ColPlan& cp = cplan[sgi];
-      if (opt.cpqr_single || cap <= 0 || 2 * cnt > cap) continue;
+      if (gram_col[sgi] || opt.cpqr_single || cap <= 0 || 2 * cnt > cap) continue;
       double wsum = 0;
       std::vector<double> wgt(cnt);
       for (int e = 0; e < cnt; ++e) {
@@ -545,6 +566,67 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       gp.scratch = off;
       gj_scratch = std::max(gj_scratch, off);
     }
+    // Gram form of the ID: per colour digit slices, exponents and G/R blocks;
+    // pivoted-Cholesky CTAs in proportion to a^3 with >= 32 columns per CTA,
+    // co-resident (cooperative) when the colour fits, else one CTA per box.
+    std::vector<GramBoxHost> gbh(use_gram ? nb : 0);
+    std::vector<ColPlan> pplan(seg_start.size());
+    int64_t gr_slices = 0, gr_expo = 0, gr_g = 0, pc_scratch = 0;
+    if (use_gram) {
+      for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+        if (!gram_col[sgi]) continue;
+        int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
+        int64_t so = 0, eo = 0, go = 0;
+        int amax = 1;
+        for (int e = b0; e < b0 + cnt; ++e) {
+          plan_gram_box(desc[e].a, desc[e].mmax, H->fp32, so, eo, go, gbh[e]);
+          amax = std::max(amax, desc[e].a);
+        }
+        gr_slices = std::max(gr_slices, so);
+        gr_expo = std::max(gr_expo, eo);
+        gr_g = std::max(gr_g, go);
+        const int cap = pchol_capacity(amax);
+        std::vector<int> P(cnt, 1);
+        int tot = cnt;
+        ColPlan& pp = pplan[sgi];
+        pp.dist = cnt <= cap;
+        if (pp.dist) {
+          double wsum = 0;
+          for (int e = b0; e < b0 + cnt; ++e) wsum += std::pow((double)desc[e].a, 3.0);
+          tot = 0;
+          for (int e = 0; e < cnt; ++e) {
+            const int a = desc[b0 + e].a;
+            const int pmax = std::max(1, (a + 31) / 32);
+            P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * std::pow((double)a, 3.0) /
+                                                              std::max(wsum, 1.0))));
+            tot += P[e];
+          }
+          while (tot > cap) {
+            int big = (int)(std::max_element(P.begin(), P.end()) - P.begin());
+            if (P[big] <= 1) break;
+            --P[big];
+            --tot;
+          }
+        }
+        pp.pbeg = (int)parts.size();
+        pp.np = tot;
+        int64_t off = 0;
+        for (int e = 0; e < cnt; ++e) {
+          for (int c = 0; c < P[e]; ++c) parts.push_back(CpqrPart{b0 + e, c, P[e], 0, off});
+          off += (int64_t)pchol_scratch_bytes(P[e]);
+        }
+        pp.scratch = off;
+        pc_scratch = std::max(pc_scratch, off);
+      }
+    }
+    std::vector<char> gram_box(nb, 0);
+    for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi)
+      for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) gram_box[e] = gram_col[sgi];
+    GramBoxHost* d_gbh = use_gram ? lw.up(gbh, st) : nullptr;
+    void* d_gr_slices = use_gram ? (void*)lw.get<uint16_t>((size_t)gr_slices) : nullptr;
+    int* d_gr_expo = use_gram ? lw.get<int>((size_t)gr_expo) : nullptr;
+    double2* d_gr_g = use_gram ? lw.get<double2>((size_t)gr_g) : nullptr;
+    unsigned char* d_pc_scratch = use_gram ? lw.get<unsigned char>((size_t)pc_scratch) : nullptr;
     // Schur update on tensor cores: per-box slice scratch (bounds), per colour
     std::vector<OzBoxHost> ozb(nb);
     std::vector<int64_t> oz_seg_slices(seg_start.size(), 0), oz_seg_expo(seg_start.size(), 0);
@@ -575,7 +657,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       launch_gather_rows(LD, b0, cnt, st);
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
-      if (cplan[sgi].dist) {
+      if (gram_col[sgi]) {
+        launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(d_pc_scratch, 0, (size_t)pplan[sgi].scratch, st));
+        CK(launch_pchol(LD, d_parts + pplan[sgi].pbeg, pplan[sgi].np, d_pc_scratch, d_gbh, d_gr_g,
+                        amax, pplan[sgi].dist, st));
+      } else if (cplan[sgi].dist) {
         CK(cudaMemsetAsync(d_cpqr_scratch, 0, (size_t)cplan[sgi].scratch, st));
         CK(launch_cpqr_dist(LD, d_parts + cplan[sgi].pbeg, cplan[sgi].np, d_cpqr_scratch, amax,
                             H->fp32, st));
@@ -619,11 +707,21 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         const BoxRun& rr = run[e];
         double a = d.a, s_ = rr.s, r_ = rr.r, n_ = rr.n;
         double m = 2.0 * rr.nq + 2.0 * opt.n_proxy;
-        double qr = 0;
-        for (int j = 0; j < rr.s; ++j) qr += 18.0 * (m - j) * (a - j - 1);
-        qr += 4.0 * s_ * s_ * r_;
         H->prof.add_work("assemble_id", 0, m * a * csz);
-        H->prof.add_work("cpqr", qr, m * a * csz);
+        if (gram_box[e]) {
+          const double ns = H->fp32 ? 4.0 : 7.0, apad = std::ceil(a / 64.0) * 64.0;
+          const double kt = std::ceil(m / 16.0) * 16.0;
+          double pc = 4.0 * s_ * s_ * r_;
+          for (int j = 0; j < rr.s; ++j) pc += 8.0 * j * (a - j - 1);
+          H->prof.add_work("gram_split", 0, m * a * csz + ns * 4.0 * apad * kt);
+          H->prof.add_work("gram", 4.0 * m * a * a, ns * 4.0 * apad * kt + 16.0 * a * a);
+          H->prof.add_work("pchol", pc, 16.0 * (a * a + a * s_ + s_ * r_));
+        } else {
+          double qr = 0;
+          for (int j = 0; j < rr.s; ++j) qr += 18.0 * (m - j) * (a - j - 1);
+          qr += 4.0 * s_ * s_ * r_;
+          H->prof.add_work("cpqr", qr, m * a * csz);
+        }
         if (rr.r == 0) continue;
         H->prof.add_work("assemble_elim", 0, 2.0 * a * (a + n_) * 16.0);
         H->prof.add_work("gemm_g1", 8.0 * r_ * (a + n_) * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));

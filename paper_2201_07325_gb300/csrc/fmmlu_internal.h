@@ -187,6 +187,25 @@ void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, v
 void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
                           int* expo, int amax, int nmax_max, int which, cudaStream_t st);
 constexpr int kOzInnerMin = 32;   // inner dimension from which the tensor-core path is used
+// Gram form of the ID (ozaki.cu, pchol.cu): G = M^H M of the ID matrix on the
+// tensor cores, then greedy pivoted Cholesky of G -- the same column selection
+// and the same R (up to row phases) as CPQR of M in exact arithmetic.
+struct GramBoxHost {     // per box of a level, planned from bounds
+  int64_t sl_off;        // bf16 offset of M's column slices: [p][part][apad][kp]
+  int64_t e_off;         // int offset of the apad column exponents
+  int64_t G_off;         // double2 offset of G (a x a), then R by columns (a x a)
+  int apad, kp;          // a padded to 64; mmax padded to 16
+};
+void plan_gram_box(int a, int mmax, bool fp32, int64_t& slice_off, int64_t& expo_off,
+                   int64_t& g_off, GramBoxHost& out);
+void launch_gram(const LevelDev& L, int b0, int nb, const GramBoxHost* d_gb, void* slices,
+                 int* expo, double2* gbuf, int amax, int mmax, bool fp32, cudaStream_t st);
+size_t pchol_scratch_bytes(int P);
+size_t pchol_smem(int amax);   // dynamic shared memory of one CTA
+int pchol_capacity(int amax);
+cudaError_t launch_pchol(const LevelDev& L, const CpqrPart* d_parts, int nparts,
+                         unsigned char* scratch, const GramBoxHost* d_gb, double2* gbuf, int amax,
+                         bool cooperative, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);

@@ -35,21 +35,27 @@ __device__ __forceinline__ int row_exponent(double m) {
   return e;
 }
 
-// v * 2^-e in (-1, 1): its first seven signed base-256 digits (each an integer
-// in [-255, 255], exact in bf16). The scaled value times 2^56 is truncated to a
-// 56-bit integer U (one exact scaling and one conversion); digit p is byte
-// 6 - p of |U| with the sign of v -- the same digits as repeatedly scaling by
-// 256 and truncating.
-__device__ __forceinline__ void split_digits(double v, int e, __nv_bfloat16* out,
-                                             int64_t stride) {
-  const long long F = (long long)ldexp(v, 56 - e);   // |F| < 2^56, truncated toward 0
+// v * 2^-e in (-1, 1): its first NS signed base-256 digits (each an integer
+// in [-255, 255], exact in bf16). The scaled value times 2^(8 NS) is truncated
+// to an integer U (one exact scaling and one conversion); digit p is byte
+// NS - 1 - p of |U| with the sign of v -- the same digits as repeatedly
+// scaling by 256 and truncating.
+template <int NS>
+__device__ __forceinline__ void split_digits_n(double v, int e, __nv_bfloat16* out,
+                                               int64_t stride) {
+  static_assert(NS >= 1 && NS <= 7, "at most 56 bits");
+  const long long F = (long long)ldexp(v, 8 * NS - e);   // |F| < 2^(8 NS), toward 0
   const bool neg = F < 0;
   const unsigned long long U = (unsigned long long)(neg ? -F : F);
 #pragma unroll
-  for (int p = 0; p < kOzSlices; ++p) {
-    int dgt = (int)((U >> (8 * (kOzSlices - 1 - p))) & 255ull);
+  for (int p = 0; p < NS; ++p) {
+    int dgt = (int)((U >> (8 * (NS - 1 - p))) & 255ull);
     out[p * stride] = __int2bfloat16_rn(neg ? -dgt : dgt);
   }
+}
+__device__ __forceinline__ void split_digits(double v, int e, __nv_bfloat16* out,
+                                             int64_t stride) {
+  split_digits_n<kOzSlices>(v, e, out, stride);
 }
 
 // One CTA per (box, 32-row chunk) of W (rows) or of X_RC (columns).
@@ -141,14 +147,15 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const __nv_bfloat16* p) {
 }
 
 // The digit-pair products of one 64 x 64 output tile: for every scale
-// d = p + q, stage A_p and B_q blocks (cp.async, double-buffered), multiply on
-// the tensor cores (exact fp32 block sums), add the pairs of equal scale as
-// int32 and accumulate each scale once in fp64. acc receives the tile of
-// sum_{p+q<=6} 2^{-8(p+q+2)} (A_p B_q) (before the row/column exponents).
-__device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv_bfloat16* Asl,
-                                                   const __nv_bfloat16* Bsl, int64_t partstride,
-                                                   int kp, int i0, int j0, int kt,
-                                                   double (&acc)[4][4][2]) {
+// d = p + q <= DMAX (digits p, q < NS), stage A_p and B_q blocks (cp.async,
+// double-buffered), multiply on the tensor cores (exact fp32 block sums), add
+// the pairs of equal scale as int32 and accumulate each scale once in fp64.
+// acc receives the tile of sum 2^{-8(p+q+2)} (op(A_p) B_q) (before the row and
+// column exponents), op = conjugation when ConjA.
+template <int NS, int DMAX, bool ConjA>
+__device__ __forceinline__ void oz_tile_acc(__nv_bfloat16* sm, const __nv_bfloat16* Asl,
+                                            const __nv_bfloat16* Bsl, int64_t partstride, int kp,
+                                            int i0, int j0, int kt, double (&acc)[4][4][2]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wr = (warp & 3) * 16;
   const int wc = (warp >> 2) * 32;
@@ -164,6 +171,8 @@ __device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv
     for (int e = 0; e < 4; ++e) acc[u][e][0] = acc[u][e][1] = 0.0;
   // stages: (d, kb, p) with q = d - p; A_p and B_q blocks double-buffered
   const int nkb = (kt + kOzKB - 1) / kOzKB;
+  auto plo = [](int d) { return d > NS - 1 ? d - (NS - 1) : 0; };
+  auto phi = [](int d) { return d < NS - 1 ? d : NS - 1; };
   auto stage = [&](int d, int kb_i, int p, int buf) {
     const int kb = kb_i * kOzKB, klen = min(kOzKB, kt - kb);
     __nv_bfloat16* dA = sm + buf * 2 * kOzStage;
@@ -174,7 +183,7 @@ __device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv
   int buf = 0;
   __syncthreads();
   stage(0, 0, 0, 0);
-  for (int d = 0; d < kOzSlices; ++d) {
+  for (int d = 0; d <= DMAX; ++d) {
     int G[4][4][2];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -183,14 +192,14 @@ __device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv
     int gcount = 0;
     const double scale = ldexp(1.0, -8 * (d + 2));
     for (int kb_i = 0; kb_i < nkb; ++kb_i) {
-      for (int p = 0; p <= d; ++p) {
+      for (int p = plo(d); p <= phi(d); ++p) {
         cp_async_wait_all();
         __syncthreads();
         // prefetch the next stage into the other buffer
         int nd = d, nk = kb_i, np = p + 1;
-        if (np > nd) { np = 0; ++nk; }
-        if (nk >= nkb) { nk = 0; ++nd; np = 0; }
-        if (nd < kOzSlices) stage(nd, nk, np, buf ^ 1);
+        if (np > phi(nd)) { np = plo(nd); ++nk; }
+        if (nk >= nkb) { nk = 0; ++nd; np = plo(nd); }
+        if (nd <= DMAX) stage(nd, nk, np, buf ^ 1);
         const __nv_bfloat16* sA = sm + buf * 2 * kOzStage;
         const __nv_bfloat16* sB = sA + kOzStage;
         const int klen = min(kOzKB, kt - kb_i * kOzKB);
@@ -213,10 +222,11 @@ __device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
               const int u = 2 * h + v;
+              // (ar + i ai)(br + i bi), or (ar - i ai)(br + i bi) when ConjA
               mma_bf16(cr[u], ar, br[2 * v], br[2 * v + 1]);
-              mma_bf16(cr[u], an, bi[2 * v], bi[2 * v + 1]);
+              mma_bf16(cr[u], ConjA ? ai : an, bi[2 * v], bi[2 * v + 1]);
               mma_bf16(ci[u], ar, bi[2 * v], bi[2 * v + 1]);
-              mma_bf16(ci[u], ai, br[2 * v], br[2 * v + 1]);
+              mma_bf16(ci[u], ConjA ? an : ai, br[2 * v], br[2 * v + 1]);
             }
           }
         }
@@ -249,6 +259,13 @@ __device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv
         acc[u][e][1] = fma((double)G[u][e][1], scale, acc[u][e][1]);
       }
   }
+}
+
+__device__ __forceinline__ void oz_tile_accumulate(__nv_bfloat16* sm, const __nv_bfloat16* Asl,
+                                                   const __nv_bfloat16* Bsl, int64_t partstride,
+                                                   int kp, int i0, int j0, int kt,
+                                                   double (&acc)[4][4][2]) {
+  oz_tile_acc<kOzSlices, kOzSlices - 1, false>(sm, Asl, Bsl, partstride, kp, i0, j0, kt, acc);
 }
 
 // one CTA per 64 x 64 tile of the box's (s+n) x (s+n) Schur update
@@ -518,6 +535,153 @@ void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, v
     attr = true;
   }
   FMMLU_LAUNCH("schur_update", st, k_oz_schur<<<gm, 256, smem, st>>>(L, b0, oz, sl, expo));
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrix G = M^H M of a box's ID matrix (m x a, column-major, ld mmax).
+// Each column of M is one row of digit slices (the contraction runs over the
+// rows of M, contiguous in memory), scaled by a power of two from its largest
+// component. complex128 columns take 7 digits and the pairs p + q <= 6 (the
+// omitted pairs are below 2^-56 of the column maxima); complex64 columns take
+// 4 digits and the pairs p + q <= 4 (below 2^-40). Every digit product and
+// every 128-term block sum is exact; the only roundings are fp64 additions.
+
+template <int NS, typename C>
+__global__ void __launch_bounds__(256) k_gram_split(LevelDev L, int b0,
+                                                    const GramBoxHost* __restrict__ gb,
+                                                    __nv_bfloat16* slices, int* expo) {
+  const int b = b0 + blockIdx.y;
+  const BoxDesc d = L.desc[b];
+  const GramBoxHost g = gb[b];
+  const int a = d.a;
+  const int m = 2 * L.run[b].nq + 2 * L.n_proxy;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * 8 + warp;       // column of M, row of the slices
+  if (k >= g.apad) return;
+  const int kt = (m + 15) & ~15;
+  const C* col = reinterpret_cast<const C*>(L.Mbuf) + d.M_off + (int64_t)k * d.mmax;
+  double mx = 0.0;
+  if (k < a)
+    for (int i = lane; i < m; i += 32) {
+      double2 v = to_d2(col[i]);
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const bool bad = !(mx <= 1.7976931348623157e308);   // inf or NaN in the column
+  if (bad) {
+    if (lane == 0) set_status(L.status, kStatusNonfinite);
+    mx = 0.0;
+  }
+  const int e = row_exponent(mx);
+  if (lane == 0) expo[g.e_off + k] = e;
+  const int64_t partstride = (int64_t)g.apad * g.kp;
+  const int64_t pstride = 2 * partstride;
+  __nv_bfloat16* dst = slices + g.sl_off + (int64_t)k * g.kp;
+  for (int i = lane; i < kt; i += 32) {
+    double2 v = make_double2(0.0, 0.0);
+    if (k < a && i < m && !bad) v = to_d2(col[i]);
+    split_digits_n<NS>(v.x, e, dst + i, pstride);
+    split_digits_n<NS>(v.y, e, dst + partstride + i, pstride);
+  }
+}
+
+// one CTA per 64 x 64 tile (tm <= tn) of the upper triangle; the lower one is
+// written as the conjugate transpose
+template <int NS, int DMAX>
+__global__ void __launch_bounds__(256) k_gram(LevelDev L, int b0, const GramBoxHost* __restrict__ gb,
+                                              const __nv_bfloat16* __restrict__ slices,
+                                              const int* __restrict__ expo, double2* gbuf) {
+  extern __shared__ __align__(16) __nv_bfloat16 sm[];
+  __shared__ int rex[64], cex[64];
+  const int b = b0 + blockIdx.y;
+  const BoxDesc d = L.desc[b];
+  const GramBoxHost g = gb[b];
+  const int a = d.a;
+  const int m = 2 * L.run[b].nq + 2 * L.n_proxy;
+  const int ta = (a + 63) / 64;
+  const int x = blockIdx.x;
+  if (x >= ta * (ta + 1) / 2) return;
+  int tn = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+  while ((tn + 1) * (tn + 2) / 2 <= x) ++tn;
+  while (tn * (tn + 1) / 2 > x) --tn;
+  const int tm = x - tn * (tn + 1) / 2;
+  const int i0 = tm * 64, j0 = tn * 64;
+  const int kt = (m + 15) & ~15;
+  if (threadIdx.x < 64) {
+    rex[threadIdx.x] = expo[g.e_off + i0 + threadIdx.x];
+    cex[threadIdx.x] = expo[g.e_off + j0 + threadIdx.x];
+  }
+  const __nv_bfloat16* sl = slices + g.sl_off;
+  double acc[4][4][2];
+  oz_tile_acc<NS, DMAX, true>(sm, sl, sl, (int64_t)g.apad * g.kp, g.kp, i0, j0, kt, acc);
+  double2* G = gbuf + g.G_off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int wr = (warp & 3) * 16, wc = (warp >> 2) * 32;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int li = wr + gq + ((e >> 1) ? 8 : 0);
+      const int lj = wc + 8 * u + 2 * tq + (e & 1);
+      const int i = i0 + li, j = j0 + lj;
+      if (i >= a || j >= a) continue;
+      const int sc = rex[li] + cex[lj];
+      const double vr = ldexp(acc[u][e][0], sc);
+      const double vi = i == j ? 0.0 : ldexp(acc[u][e][1], sc);
+      G[i + (int64_t)j * a] = make_double2(vr, vi);
+      if (tm != tn) G[j + (int64_t)i * a] = make_double2(vr, -vi);
+    }
+}
+
+constexpr int kGramNS64 = 7, kGramNS32 = 4;
+
+void plan_gram_box(int a, int mmax, bool fp32, int64_t& slice_off, int64_t& expo_off,
+                   int64_t& g_off, GramBoxHost& out) {
+  const int ns = fp32 ? kGramNS32 : kGramNS64;
+  out.apad = (a + 63) & ~63;
+  out.kp = (mmax + 15) & ~15;
+  out.sl_off = slice_off;
+  out.e_off = expo_off;
+  out.G_off = g_off;
+  slice_off += (int64_t)ns * 2 * out.apad * out.kp;
+  expo_off += out.apad;
+  g_off += 2 * (int64_t)a * a;
+}
+
+void launch_gram(const LevelDev& L, int b0, int nb, const GramBoxHost* d_gb, void* slices,
+                 int* expo, double2* gbuf, int amax, int mmax, bool fp32, cudaStream_t st) {
+  if (nb <= 0) return;
+  __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(slices);
+  const int apad = (amax + 63) & ~63;
+  dim3 gs((unsigned)(apad / 8), nb);
+  const size_t smem = (size_t)4 * kOzStage * sizeof(__nv_bfloat16);
+  const int ta = apad / 64;
+  dim3 gm((unsigned)(ta * (ta + 1) / 2), nb);
+  (void)mmax;
+  if (fp32) {
+    FMMLU_LAUNCH("gram_split", st,
+                 (k_gram_split<kGramNS32, float2><<<gs, 256, 0, st>>>(L, b0, d_gb, sl, expo)));
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gram<kGramNS32, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      attr = true;
+    }
+    FMMLU_LAUNCH("gram", st,
+                 (k_gram<kGramNS32, 4><<<gm, 256, smem, st>>>(L, b0, d_gb, sl, expo, gbuf)));
+  } else {
+    FMMLU_LAUNCH("gram_split", st,
+                 (k_gram_split<kGramNS64, double2><<<gs, 256, 0, st>>>(L, b0, d_gb, sl, expo)));
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gram<kGramNS64, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      attr = true;
+    }
+    FMMLU_LAUNCH("gram", st,
+                 (k_gram<kGramNS64, 6><<<gm, 256, smem, st>>>(L, b0, d_gb, sl, expo, gbuf)));
+  }
 }
 
 }  // namespace fmmlu

@@ -172,6 +172,31 @@ def test_schur_emulation_exact_limit_and_accuracy(pkg, ell, emul):
     assert np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[0]) <= 1e-7
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gram_id_matches_householder_id(pkg, ell, prec):
+    """The ID by pivoted Cholesky of G = M^H M (G formed exactly on the tensor
+    cores) and by Householder CPQR of M make the same greedy selection (Def.
+    ID) in exact arithmetic: per-level ranks agree up to near-tied pivots and
+    both factorizations solve within 10 eps of the dense solution."""
+    s, A, b, xd = ell
+    eps = 1e-6 if prec == "fp64" else 1e-4
+    P = pkg.PRECISION_FP64 if prec == "fp64" else pkg.PRECISION_MIXED
+    out = {}
+    for method, name in ((pkg.ID_HOUSEHOLDER, "householder"), (pkg.ID_GRAM, "gram")):
+        fac = _gpu_factor(pkg, s, K, eps, leaf_size=24, precision=P, id_method=method)
+        st = fac.stats()
+        x = fac.solve(torch.from_numpy(b)).cpu().numpy()
+        fac.free()
+        assert st["id_method"] == name
+        assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 10 * eps
+        assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 10 * eps
+        out[name] = st
+    for lh, lg in zip(out["householder"]["levels"], out["gram"]["levels"]):
+        assert lh["level"] == lg["level"] and lh["boxes"] == lg["boxes"]
+        assert abs(lh["sum_s"] - lg["sum_s"]) <= max(2, 0.01 * lh["sum_s"])
+    assert abs(out["householder"]["n0"] - out["gram"]["n0"]) <= max(4, 0.02 * out["gram"]["n0"])
+
+
 def test_single_box_is_dense_lu(pkg):
     s = synth.ellipsoid_uniform(50, seed=3)
     A = kernel.dense_matrix(s.points, s.normals, s.weights, 3.0, 3.0)
