@@ -123,6 +123,24 @@ class ClockSampler:
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+def is_tensor_kernel(name: str) -> bool:
+    """Kernels whose flops are bf16 tensor-core products (exact digit split)."""
+    return name.endswith("_tc") or name == "gram"
+
+
+def measured_peaks() -> dict:
+    """Roofline denominators: the measured copy bandwidth and cuBLAS bf16 rate
+    of this GPU type (MEASURED_PEAKS.json), else the profiling fallback."""
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"hbm": (float(m["hbm_gbs"]), "of measured hbm_gbs"),
+                "bf16_sustained": (float(m["bf16_tflops_sustained"]),
+                                   "of measured bf16_tflops_sustained (kernel timed inside a long step)")}
+    except Exception:
+        return {"hbm": (6800.0, "of fallback (6.8 TB/s)"),
+                "bf16_sustained": (1700.0, "of fallback (1.7 PFLOP/s sustained)")}
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2201_07325_gb300", "csrc")
@@ -294,7 +312,15 @@ def run_gpu(args, rank, world):
     fp32_path = precision == pkg.PRECISION_MIXED or (precision == pkg.PRECISION_AUTO
                                                      and eps >= 1e-5)
     fp32_kernels = {"cpqr", "assemble_id"} if fp32_path else set()
-    if d["flops"] > 0:
+    peaks = measured_peaks()
+    if is_tensor_kernel(dname):
+        # exact-split products on the bf16 tensor cores: the bf16 flops of the
+        # digit-pair products against the measured sustained bf16 rate
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        peak, src = peaks["bf16_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": dname, "peak_source": src}
+    elif d["flops"] > 0:
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         peak = FP32_PEAK_TFLOPS if dname in fp32_kernels else FP64_PEAK_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -303,9 +329,9 @@ def run_gpu(args, rank, world):
                 else "nominal fp64 of the profiling recipe (1.25 TFLOP/s)"}
     else:
         gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        peak = 6783.5
+        peak, src = peaks["hbm"]
         roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                "frac": gbs / peak, "kernel": dname, "peak_source": "measured hbm_gbs"}
+                "frac": gbs / peak, "kernel": dname, "peak_source": src}
     tr = recorded_traffic(dname, args.workload)
     roof["traffic"] = tr
     roof["avg_launch_ms"] = d["ms"] / max(1, d["launches"])
@@ -332,7 +358,10 @@ def run_gpu(args, rank, world):
         "roofline": roof,
         "top_kernels": {nm: {"ms_per_step": e["ms"] / args.steps,
                              "launches_per_step": e["launches"] / args.steps,
-                             "tflops": (e["flops"] / (e["ms"] / 1e3) / 1e12) if e["ms"] else 0}
+                             "tflops": (e["flops"] / (e["ms"] / 1e3) / 1e12) if e["ms"] else 0,
+                             "unit": "bf16 TFLOP/s" if is_tensor_kernel(nm) else
+                                     ("TFLOP/s" if e["flops"] else "GB/s"),
+                             "gbs": (e["bytes"] / (e["ms"] / 1e3) / 1e9) if e["ms"] else 0}
                         for nm, e in top},
         "clocks": clocks,
     }
@@ -400,6 +429,29 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def factor_once(args) -> dict:
+    """One tree + factorization of the workload (optionally at another size)
+    with per-launch profiling on: the small case the ncu captures run."""
+    import torch
+    import paper_2201_07325_gb300 as pkg
+    pkg.load_library()
+    spec = synth.WORKLOADS[args.workload]
+    s = synth.make_surface(args.workload, args.n)
+    prec = {"fp64": pkg.PRECISION_FP64, "mixed": pkg.PRECISION_MIXED,
+            "auto": pkg.PRECISION_AUTO}[args.precision]
+    opts = pkg.fmmlu_default_opts(precision=prec, profile=1)
+    pts, nrm, w = (torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                   for a in (s.points, s.normals, s.weights))
+    t = pkg.fmmlu_build_tree(pts, opts)
+    h = pkg.fmmlu_factor(t, pts, nrm, w, spec["k"], spec["eps"], opts)
+    torch.cuda.synchronize()
+    st = pkg.fmmlu_stats(h)
+    pkg.fmmlu_free(h)
+    pkg.fmmlu_free(t)
+    return {"workload": args.workload, "n": s.n, "precision": args.precision, "n0": st["n0"],
+            "kernels": st["kernels"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,9 +461,17 @@ def main():
     ap.add_argument("--workload", default="ellipsoid50k", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--factor-once", action="store_true",
+                    help="one profiled tree + factor of the workload (ncu captures); "
+                         "prints the per-kernel algorithmic flops/bytes")
+    ap.add_argument("--n", type=int, default=None,
+                    help="with --factor-once: the same surface family at n points")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.factor_once:
+        print(json.dumps(factor_once(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -714,7 +714,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           double pc = 4.0 * s_ * s_ * r_;
           for (int j = 0; j < rr.s; ++j) pc += 8.0 * j * (a - j - 1);
           H->prof.add_work("gram_split", 0, m * a * csz + ns * 4.0 * apad * kt);
-          H->prof.add_work("gram", 4.0 * m * a * a, ns * 4.0 * apad * kt + 16.0 * a * a);
+          // bf16 tensor flops of the upper-triangle tiles: digit pairs x 4 real
+          // products x 2 flops x m x a (a + 1) / 2
+          const double pairs = H->fp32 ? 13.0 : 28.0;
+          H->prof.add_work("gram", pairs * 8.0 * m * a * (a + 1) / 2.0,
+                           ns * 4.0 * apad * kt + 16.0 * a * a);
           H->prof.add_work("pchol", pc, 16.0 * (a * a + a * s_ + s_ * r_));
         } else {
           double qr = 0;
@@ -724,13 +728,24 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         }
         if (rr.r == 0) continue;
         H->prof.add_work("assemble_elim", 0, 2.0 * a * (a + n_) * 16.0);
-        H->prof.add_work("gemm_g1", 8.0 * r_ * (a + n_) * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
-        H->prof.add_work("gemm_g3", 8.0 * (a + n_) * r_ * s_, 16.0 * (s_ * r_ + 2 * a * (a + n_)));
+        // complex products: 8 fp64 flops per multiply-add on the FMA path; on
+        // the tensor-core path (inner dimension >= kOzInnerMin) 28 digit pairs
+        // x 4 real bf16 products x 2 flops, and the digit split of the operands
+        const bool tc_s = use_oz && rr.s >= kOzInnerMin, tc_r = use_oz && rr.r >= kOzInnerMin;
+        const double c_tc = 28.0 * 4.0 * 2.0, split_b = 16.0 + 28.0;   // split: read fp64, write digits
+        H->prof.add_work(tc_s ? "gemm_g1_tc" : "gemm_g1", (tc_s ? c_tc : 8.0) * r_ * (a + n_) * s_,
+                         16.0 * (s_ * r_ + 2 * a * (a + n_)));
+        H->prof.add_work(tc_s ? "gemm_g3_tc" : "gemm_g3", (tc_s ? c_tc : 8.0) * (a + n_) * r_ * s_,
+                         16.0 * (s_ * r_ + 2 * a * (a + n_)));
+        if (tc_s) H->prof.add_work("oz_split", 0, 2.0 * split_b * (r_ * s_ + s_ * (a + n_)));
         H->prof.add_work("gemm_xrr", 8.0 * r_ * r_ * s_, 16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
         H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
-        H->prof.add_work("gemm_w", 8.0 * (s_ + n_) * r_ * r_, 16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
-        H->prof.add_work("schur_update", 8.0 * (s_ + n_) * (s_ + n_) * r_,
+        H->prof.add_work(tc_r ? "gemm_w_tc" : "gemm_w", (tc_r ? c_tc : 8.0) * (s_ + n_) * r_ * r_,
+                         16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
+        H->prof.add_work(tc_r ? "schur_tc" : "schur_update",
+                         (tc_r ? c_tc : 8.0) * (s_ + n_) * (s_ + n_) * r_,
                          16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));
+        if (tc_r) H->prof.add_work("oz_split", 0, split_b * (2 * (s_ + n_) * r_ + 2 * r_ * r_));
       }
     }
     // solve plan for this level

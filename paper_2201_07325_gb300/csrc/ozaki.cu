@@ -495,9 +495,9 @@ void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_
                           int* expo, int amax, int nmax_max, int which, cudaStream_t st) {
   if (nb <= 0) return;
   __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(slices);
-  if (which == 0) launch_ozg<ProbG1>("gemm_g1", L, b0, nb, d_oz, sl, expo, amax, amax + nmax_max, st);
-  if (which == 1) launch_ozg<ProbG3>("gemm_g3", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
-  if (which == 2) launch_ozg<ProbW>("gemm_w", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
+  if (which == 0) launch_ozg<ProbG1>("gemm_g1_tc", L, b0, nb, d_oz, sl, expo, amax, amax + nmax_max, st);
+  if (which == 1) launch_ozg<ProbG3>("gemm_g3_tc", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
+  if (which == 2) launch_ozg<ProbW>("gemm_w_tc", L, b0, nb, d_oz, sl, expo, amax + nmax_max, amax, st);
 }
 
 size_t oz_slice_elems(int a, int nmax) {
@@ -534,7 +534,7 @@ void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, v
     cudaFuncSetAttribute(k_oz_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  FMMLU_LAUNCH("schur_update", st, k_oz_schur<<<gm, 256, smem, st>>>(L, b0, oz, sl, expo));
+  FMMLU_LAUNCH("schur_tc", st, k_oz_schur<<<gm, 256, smem, st>>>(L, b0, oz, sl, expo));
 }
 
 // ---------------------------------------------------------------------------
