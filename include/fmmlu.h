@@ -91,11 +91,18 @@ typedef struct fmmlu_opts {
                                  (reported by fmmlu_stats). Default 0.      */
   int cpqr_single;            /* 1: run every pivoted QR with one CTA per box
                                  (no row distribution). Default 0.          */
-  int schur_emulation;        /* 1 (default): Schur-complement products on the
-                                 bf16 tensor cores by an exact 7-digit
-                                 splitting of the complex128 operands (every
-                                 product exact, every rounding an fp64
-                                 addition); 0: fp64 FMA. */
+  int schur_emulation;        /* products of the elimination (G1, G3, W,
+                                 Schur update) with an inner dimension >= 32,
+                                 and the Gram matrix of the ID:
+                                 1 (default): tcgen05 tensor cores (TMEM
+                                 accumulators) on an exact split of each
+                                 complex128 operand into 7 bf16 digits; every
+                                 digit product and partial sum is an exact
+                                 integer, the only rounding is the final
+                                 conversion to double;
+                                 2: the same split on mma.sync tensor-core
+                                 instructions (fp64 accumulation);
+                                 0: fp64 FMA (Gram matrix as in 1). */
   int id_method;              /* FMMLU_ID_*: how the ID of Def. ID picks its
                                  skeleton (the same greedy column selection
                                  either way). Default FMMLU_ID_AUTO.        */

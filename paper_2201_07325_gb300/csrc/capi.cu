@@ -125,6 +125,7 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (o.precision < 0 || o.precision > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad precision");
   if (!(o.eps_id_divisor > 0.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps_id_divisor must be > 0");
   if (o.id_method < 0 || o.id_method > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad id_method");
+  if (o.schur_emulation < 0 || o.schur_emulation > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad schur_emulation");
   return o;
 }
 
@@ -569,21 +570,26 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     // Gram form of the ID: per colour digit slices, exponents and G/R blocks;
     // pivoted-Cholesky CTAs in proportion to a^3 with >= 32 columns per CTA,
     // co-resident (cooperative) when the colour fits, else one CTA per box.
+    // G = M^H M on tcgen05 (default) or on the mma.sync path (schur_emulation 2)
+    const bool gram_tc = opt.schur_emulation != 2;
     std::vector<GramBoxHost> gbh(use_gram ? nb : 0);
+    std::vector<TcBoxHost> gtb(use_gram && gram_tc ? nb : 0);
     std::vector<ColPlan> pplan(seg_start.size());
     int64_t gr_slices = 0, gr_expo = 0, gr_g = 0, pc_scratch = 0;
     if (use_gram) {
       for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
         if (!gram_col[sgi]) continue;
         int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
-        int64_t so = 0, eo = 0, go = 0;
+        int64_t so = 0, eo = 0, go = 0, tso = 0, teo = 0;
         int amax = 1;
         for (int e = b0; e < b0 + cnt; ++e) {
           plan_gram_box(desc[e].a, desc[e].mmax, H->fp32, so, eo, go, gbh[e]);
+          if (gram_tc)
+            plan_tc_box(desc[e].a, desc[e].a, desc[e].mmax, H->fp32 ? 4 : 7, tso, teo, gtb[e]);
           amax = std::max(amax, desc[e].a);
         }
-        gr_slices = std::max(gr_slices, so);
-        gr_expo = std::max(gr_expo, eo);
+        gr_slices = std::max(gr_slices, gram_tc ? tso : 2 * so);   // bytes
+        gr_expo = std::max(gr_expo, gram_tc ? teo : eo);
         gr_g = std::max(gr_g, go);
         const int cap = pchol_capacity(amax);
         std::vector<int> P(cnt, 1);
@@ -623,7 +629,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi)
       for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) gram_box[e] = gram_col[sgi];
     GramBoxHost* d_gbh = use_gram ? lw.up(gbh, st) : nullptr;
-    void* d_gr_slices = use_gram ? (void*)lw.get<uint16_t>((size_t)gr_slices) : nullptr;
+    TcBoxHost* d_gtb = use_gram && gram_tc ? lw.up(gtb, st) : nullptr;
+    void* d_gr_slices = use_gram ? (void*)lw.get<unsigned char>((size_t)gr_slices) : nullptr;
     int* d_gr_expo = use_gram ? lw.get<int>((size_t)gr_expo) : nullptr;
     double2* d_gr_g = use_gram ? lw.get<double2>((size_t)gr_g) : nullptr;
     unsigned char* d_pc_scratch = use_gram ? lw.get<unsigned char>((size_t)pc_scratch) : nullptr;
@@ -632,7 +639,24 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     std::vector<int64_t> oz_seg_slices(seg_start.size(), 0), oz_seg_expo(seg_start.size(), 0);
     int64_t oz_slices = 0, oz_expo = 0;
     const bool use_oz = opt.schur_emulation != 0;
-    if (use_oz) {
+    const bool use_tc = opt.schur_emulation == 1;    // tcgen05; 2 = mma.sync
+    // tcgen05 elimination products (G1, G3, W, Schur): operand bounds per box
+    std::vector<TcBoxHost> tcb(use_tc ? nb : 0);
+    int64_t tc_slices = 0, tc_expo = 0;
+    if (use_tc) {
+      for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+        int64_t so = 0, eo = 0;
+        for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e)
+          plan_tc_box(desc[e].a + desc[e].nmax, desc[e].a + desc[e].nmax, desc[e].a, 7, so, eo,
+                      tcb[e]);
+        tc_slices = std::max(tc_slices, so);
+        tc_expo = std::max(tc_expo, eo);
+      }
+    }
+    TcBoxHost* d_tcb = use_tc ? lw.up(tcb, st) : nullptr;
+    void* d_tc_slices = use_tc ? (void*)lw.get<unsigned char>((size_t)tc_slices) : nullptr;
+    int* d_tc_expo = use_tc ? lw.get<int>((size_t)tc_expo) : nullptr;
+    if (use_oz && !use_tc) {
       for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
         int64_t so = 0, eo = 0;
         for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e)
@@ -641,9 +665,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         oz_expo = std::max(oz_expo, eo);
       }
     }
-    OzBoxHost* d_ozb = use_oz ? lw.up(ozb, st) : nullptr;
-    void* d_oz_slices = use_oz ? (void*)lw.get<uint16_t>((size_t)oz_slices) : nullptr;
-    int* d_oz_expo = use_oz ? lw.get<int>((size_t)oz_expo) : nullptr;
+    const bool use_mma = use_oz && !use_tc;
+    OzBoxHost* d_ozb = use_mma ? lw.up(ozb, st) : nullptr;
+    void* d_oz_slices = use_mma ? (void*)lw.get<uint16_t>((size_t)oz_slices) : nullptr;
+    int* d_oz_expo = use_mma ? lw.get<int>((size_t)oz_expo) : nullptr;
     CpqrPart* d_parts = lw.up(parts, st);
     unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
     unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
@@ -658,7 +683,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       launch_gather_rows(LD, b0, cnt, st);
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
       if (gram_col[sgi]) {
-        launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
+        if (gram_tc)
+          launch_tc_gram(LD, b0, cnt, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g, amax,
+                         H->fp32, st);
+        else
+          launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
         CK(cudaGetLastError());
         CK(cudaMemsetAsync(d_pc_scratch, 0, (size_t)pplan[sgi].scratch, st));
         CK(launch_pchol(LD, d_parts + pplan[sgi].pbeg, pplan[sgi].np, d_pc_scratch, d_gbh, d_gr_g,
@@ -674,7 +703,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       const int kskip = use_oz ? kOzInnerMin : 0;
       launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
       launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
-      if (use_oz) {
+      if (use_tc) {
+        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 0, st);
+        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 1, st);
+      } else if (use_oz) {
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 0, st);
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 1, st);
       }
@@ -686,10 +718,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_xrr_inverse(LD, b0, cnt, amax, st);
       }
       launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
-      if (use_oz)
+      if (use_tc)
+        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 2, st);
+      else if (use_oz)
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 2, st);
       launch_schur_update(LD, b0, cnt, amax, nmaxm, st, kskip);
-      if (use_oz)
+      if (use_tc)
+        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 3, st);
+      else if (use_oz)
         launch_oz_schur(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, st);
       CK(cudaGetLastError());
     }
@@ -713,7 +749,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           const double kt = std::ceil(m / 16.0) * 16.0;
           double pc = 4.0 * s_ * s_ * r_;
           for (int j = 0; j < rr.s; ++j) pc += 8.0 * j * (a - j - 1);
-          H->prof.add_work("gram_split", 0, m * a * csz + ns * 4.0 * apad * kt);
+          H->prof.add_work(gram_tc ? "tc_split" : "gram_split", 0, m * a * csz + ns * 4.0 * apad * kt);
           // bf16 tensor flops of the upper-triangle tiles: digit pairs x 4 real
           // products x 2 flops x m x a (a + 1) / 2
           const double pairs = H->fp32 ? 13.0 : 28.0;
@@ -737,7 +773,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                          16.0 * (s_ * r_ + 2 * a * (a + n_)));
         H->prof.add_work(tc_s ? "gemm_g3_tc" : "gemm_g3", (tc_s ? c_tc : 8.0) * (a + n_) * r_ * s_,
                          16.0 * (s_ * r_ + 2 * a * (a + n_)));
-        if (tc_s) H->prof.add_work("oz_split", 0, 2.0 * split_b * (r_ * s_ + s_ * (a + n_)));
+        const char* split_name = use_tc ? "tc_split" : "oz_split";
+        if (tc_s) H->prof.add_work(split_name, 0, 2.0 * split_b * (r_ * s_ + s_ * (a + n_)));
         H->prof.add_work("gemm_xrr", 8.0 * r_ * r_ * s_, 16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
         H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
         H->prof.add_work(tc_r ? "gemm_w_tc" : "gemm_w", (tc_r ? c_tc : 8.0) * (s_ + n_) * r_ * r_,
@@ -745,7 +782,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         H->prof.add_work(tc_r ? "schur_tc" : "schur_update",
                          (tc_r ? c_tc : 8.0) * (s_ + n_) * (s_ + n_) * r_,
                          16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));
-        if (tc_r) H->prof.add_work("oz_split", 0, split_b * (2 * (s_ + n_) * r_ + 2 * r_ * r_));
+        if (tc_r) H->prof.add_work(split_name, 0, split_b * (2 * (s_ + n_) * r_ + 2 * r_ * r_));
       }
     }
     // solve plan for this level

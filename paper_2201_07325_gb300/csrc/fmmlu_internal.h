@@ -206,6 +206,21 @@ int pchol_capacity(int amax);
 cudaError_t launch_pchol(const LevelDev& L, const CpqrPart* d_parts, int nparts,
                          unsigned char* scratch, const GramBoxHost* d_gb, double2* gbuf, int amax,
                          bool cooperative, cudaStream_t st);
+// tcgemm.cu: exact-split complex products on tcgen05 tensor cores (TMEM
+// accumulators, bulk-copy operand pipeline)
+struct TcBoxHost {       // per box of a colour, planned from bounds
+  int64_t a_off, b_off;  // byte offsets of the A and B digit slices
+  int64_t ea_off, eb_off;  // int offsets of the row / column exponents
+};
+void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_t& expo_off,
+                 TcBoxHost& out);
+size_t tc_smem_bytes(int ns);
+// which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}, 3 = Schur update
+void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
+                    int* expo, int amax, int nmax_max, int which, cudaStream_t st);
+void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
+                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, bool fp32,
+                    cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);

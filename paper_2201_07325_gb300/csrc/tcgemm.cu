@@ -1,0 +1,607 @@
+// Exactly split complex products on the fifth-generation tensor cores
+// (tcgen05.mma with accumulators in tensor memory, operands staged by bulk
+// copies).
+//
+// C = op(A) B (A m x k, B k x n, complex128 or complex64; op = identity or
+// conjugation) is formed as follows. Every row of A and every column of B is
+// scaled by a power of two 2^e taken from its largest component and written as
+// NS balanced base-256 digits c_0 .. c_{NS-1} in [-128, 128], exact in bf16:
+//     v ~ 2^e sum_p c_p 2^{-8(p+1)}        (the leading 8 NS - 1 bits of v/2^e).
+// Then C_ij = 2^{e_i + e_j - 16} sum_{d <= DMAX} 2^{-8d} S_d(i, j), where S_d is
+// the integer matrix sum_{p+q=d} op(A_p) B_q. Each S_d has its own fp32
+// accumulator in tensor memory; it is read out (into 64-bit integers) after a
+// window of W_d k16-steps with W_d (pairs in the group) <= 32, so every partial
+// sum is an integer of magnitude <= 2^24 and exact in fp32. The only rounding is
+// the final conversion of the integers to double.
+//
+// One CTA computes a 128 x 32 complex tile. A complex product is two MMAs of
+// N = 64: B is staged as three 32-row parts, [-Bi | Br | Bi] (or [Br | Bi | -Br]
+// for conj(A)), so that A_re x [Br ; Bi] + A_im x [-Bi ; Br] = [Cr | Ci].
+// Warp roles: warp 0 issues the bulk copies of the two-stage operand pipeline,
+// warp 1 owns tensor memory and issues the MMAs (one thread), warps 2..9 drain
+// the accumulators (warp w reads tensor-memory lanes 32 (w % 4) .. + 31).
+// Every wait is bounded; on a timeout the CTA records kStatusTimeout, lets its
+// copies and MMAs in flight finish (bounded), frees tensor memory and returns.
+//
+// Global layouts written by the split kernels (both per box, k in steps of 16):
+//   A: [row block of 128][k16 step][digit p][part re, im][128 x 16 bf16]
+//   B: [column block of 32][k16 step][digit q][96 x 16 bf16 (three parts)]
+// where a 128 x 16 (96 x 16) block is in the K-major core-matrix order of the
+// MMA's shared-memory descriptor: 8 x 8 core matrices of 128 contiguous bytes,
+// row groups 128 B apart, the two k halves 2048 B (1536 B) apart.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+
+namespace fmmlu {
+
+namespace tc {
+
+constexpr int kThreads = 320;
+constexpr int kRows = 128;                      // tile rows (MMA M)
+constexpr int kCols = 32;                       // complex tile columns (MMA N = 64)
+constexpr int kAChunk = kRows * 16 * 2;         // one digit part of A, one k16 step
+constexpr int kBChunk = 3 * kCols * 16 * 2;     // one digit of B (three parts)
+constexpr long long kWaitLimit = 20000000;      // polls (~1-2 s)
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint64_t* b, uint32_t par) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(par)
+      : "memory");
+  return ok;
+}
+// bounded wait; false on timeout or when another thread of the CTA gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t par, volatile int* abort_flag) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(b, par)) return true;
+    if ((i & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of tcgen05
+  return d;
+}
+// instruction descriptor of kind::f16: bf16 A and B (K-major), fp32 D
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc(kRows, 2 * kCols)), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (r, k) in a rows x 16 block in core-matrix order
+__device__ __forceinline__ int canon16(int r, int k, int rows) {
+  return ((k >> 3) * (rows >> 3) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// digit pairs of group d and window lengths (k16 steps)
+__host__ __device__ constexpr int plo(int d, int ns) { return d > ns - 1 ? d - (ns - 1) : 0; }
+__host__ __device__ constexpr int phi(int d, int ns) { return d < ns - 1 ? d : ns - 1; }
+__host__ __device__ constexpr int window(int d, int ns) { return 32 / (phi(d, ns) - plo(d, ns) + 1); }
+
+// balanced base-256 digits of v / 2^e (|v| < 2^(e-1)): NS of them, c_0 first
+template <int NS>
+__device__ __forceinline__ void balanced_digits(double v, int e, int* c) {
+  long long F = (long long)ldexp(v, 8 * NS - e);   // |F| < 2^(8 NS - 1), toward zero
+#pragma unroll
+  for (int i = NS - 1; i >= 1; --i) {
+    int low = (int)(F & 255);
+    if (low >= 128) low -= 256;
+    c[i] = low;
+    F = (F - low) >> 8;
+  }
+  c[0] = (int)F;
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// problems: sizes of one box, element accessors of op-free A (m x k) and
+// B (k x n), and the epilogue
+
+struct TcExtra {
+  const GramBoxHost* gb;
+  double2* gbuf;
+};
+
+struct TcSchur {    // Delta(S|N, S|N) -= W X_RC: (s+n) x (s+n) x r
+  static constexpr bool kConj = false, kUpper = false;
+  __device__ static bool dims(const LevelDev&, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.s + rr.n; n = m; k = rr.r; return rr.r >= kOzInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.Wbuf[d.W_off + i + (int64_t)kk * (d.a + d.nmax)];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int kk, int j) {
+    return L.arena[d.G1_off + rr.s + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const int s = rr.s;
+    const int* perm = L.iarena + d.idx_off + d.a + d.nmax;
+    const int* ndof = L.rows + d.rows_off + 3 * d.qmax;
+    const int* npos = ndof + d.nmax;
+    const int* nloc = npos + d.nmax;
+    const int xl = i < s ? 0 : nloc[i - s], xp = i < s ? perm[i] : npos[i - s];
+    const int yl = j < s ? 0 : nloc[j - s], yp = j < s ? perm[j] : npos[j - s];
+    const int cnt = 1 + d.ncnt;
+    const int64_t off = L.pairtab[d.pairtab + (int64_t)xl * cnt + yl];
+    if (off < 0) { set_status(L.status, kStatusBound); return; }
+    const int ld = xl == 0 ? d.a : L.cur_a0[L.nlist[d.nbeg + xl - 1]];
+    double2* pz = L.delta + off + xp + (int64_t)yp * ld;
+    const double2 c = *pz;
+    *pz = make_double2(c.x - vr, c.y - vi);
+  }
+};
+
+struct TcW {        // W = X_CR X_RR^{-1}: (s+n) x r x r, stored
+  static constexpr bool kConj = false, kUpper = false;
+  __device__ static bool dims(const LevelDev&, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.s + rr.n; n = rr.r; k = rr.r; return rr.r >= kOzInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int kk) {
+    return L.arena[d.G3_off + i + (int64_t)(rr.s + kk) * (d.a + d.nmax)];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.Xinv_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    L.Wbuf[d.W_off + i + (int64_t)j * (d.a + d.nmax)] = make_double2(vr, vi);
+  }
+};
+
+struct TcG1 {       // G1[s:a, :] -= T^T G1[0:s, :]: r x (a+n) x s
+  static constexpr bool kConj = false, kUpper = false;
+  __device__ static bool dims(const LevelDev&, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.r; n = d.a + rr.n; k = rr.s; return rr.r > 0 && rr.s >= kOzInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.arena[d.T_off + kk + (int64_t)i * d.a];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.G1_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    double2* c = L.arena + d.G1_off + (rr.s + i) + (int64_t)j * d.a;
+    const double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
+};
+
+struct TcG3 {       // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
+  static constexpr bool kConj = false, kUpper = false;
+  __device__ static bool dims(const LevelDev&, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = d.a + rr.n; n = rr.r; k = rr.s; return rr.r > 0 && rr.s >= kOzInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.arena[d.G3_off + i + (int64_t)kk * (d.a + d.nmax)];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.T_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    double2* c = L.arena + d.G3_off + i + (int64_t)(rr.s + j) * (d.a + d.nmax);
+    const double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
+};
+
+// G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
+template <typename CM>
+struct TcGram {
+  static constexpr bool kConj = true, kUpper = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int& m,
+                              int& n, int& k) {
+    m = d.a; n = d.a; k = 2 * rr.nq + 2 * L.n_proxy; return d.a > 0;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return to_d2(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)i * d.mmax]);
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return to_d2(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)j * d.mmax]);
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra& x,
+                             int i, int j, double vr, double vi) {
+    if (i > j) return;   // the lower triangle is written as the mirror
+    const int b = (int)(&d - L.desc);
+    double2* G = x.gbuf + x.gb[b].G_off;
+    const int a = d.a;
+    G[i + (int64_t)j * a] = make_double2(vr, i == j ? 0.0 : vi);
+    if (i < j) G[j + (int64_t)i * a] = make_double2(vr, -vi);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// split kernels: one warp per row of A (side 0) or column of B (side 1)
+
+template <class Prob, int NS>
+__global__ void __launch_bounds__(256) k_tc_split(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+                                                  unsigned char* slices, int* expo) {
+  const int b = b0 + blockIdx.z;
+  const BoxDesc& d = L.desc[b];
+  const BoxRun rr = L.run[b];
+  int m, n, k;
+  if (!Prob::dims(L, d, rr, m, n, k)) return;
+  const TcBoxHost t = tb[blockIdx.z];
+  const bool side_b = blockIdx.y == 1;
+  const int len = side_b ? n : m;
+  const int lpad = side_b ? (n + tc::kCols - 1) / tc::kCols * tc::kCols
+                          : (m + tc::kRows - 1) / tc::kRows * tc::kRows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= lpad) return;
+  const int KS = (k + 15) / 16;
+  double mx = 0.0;
+  if (row < len)
+    for (int kk = lane; kk < k; kk += 32) {
+      const double2 v = side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const bool bad = !(mx <= 1.7976931348623157e308);
+  if (bad) {
+    if (lane == 0) set_status(L.status, kStatusNonfinite);
+    mx = 0.0;
+  }
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);   // mx < 2^e
+    e += 1;          // |v| < 2^(e-1): the leading balanced digit stays in [-128, 128]
+  }
+  if (lane == 0) expo[(side_b ? t.eb_off : t.ea_off) + row] = e;
+  unsigned char* base = slices + (side_b ? t.b_off : t.a_off);
+  const int blk = side_b ? row / tc::kCols : row / tc::kRows;
+  const int r = side_b ? row % tc::kCols : row % tc::kRows;
+  for (int kk = lane; kk < KS * 16; kk += 32) {
+    double2 v = make_double2(0.0, 0.0);
+    if (row < len && kk < k && !bad)
+      v = side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
+    int cr[NS], ci[NS];
+    tc::balanced_digits<NS>(v.x, e, cr);
+    tc::balanced_digits<NS>(v.y, e, ci);
+    const int ks = kk >> 4, kq = kk & 15;
+    if (!side_b) {
+      unsigned char* step = base + ((int64_t)blk * KS + ks) * (2 * NS) * tc::kAChunk;
+      const int off = tc::canon16(r, kq, tc::kRows);
+#pragma unroll
+      for (int p = 0; p < NS; ++p) {
+        *reinterpret_cast<__nv_bfloat16*>(step + (2 * p) * tc::kAChunk + off) = __int2bfloat16_rn(cr[p]);
+        *reinterpret_cast<__nv_bfloat16*>(step + (2 * p + 1) * tc::kAChunk + off) =
+            __int2bfloat16_rn(ci[p]);
+      }
+    } else {
+      unsigned char* step = base + ((int64_t)blk * KS + ks) * NS * tc::kBChunk;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        unsigned char* dg = step + q * tc::kBChunk;
+        // three 32-row parts: [-im | re | im], or [re | im | -re] for conj(A)
+        const int p0 = Prob::kConj ? cr[q] : -ci[q];
+        const int p1 = Prob::kConj ? ci[q] : cr[q];
+        const int p2 = Prob::kConj ? -cr[q] : ci[q];
+        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r, kq, 3 * tc::kCols)) = __int2bfloat16_rn(p0);
+        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r + tc::kCols, kq, 3 * tc::kCols)) =
+            __int2bfloat16_rn(p1);
+        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r + 2 * tc::kCols, kq, 3 * tc::kCols)) =
+            __int2bfloat16_rn(p2);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the product: one CTA per 128 x 32 complex tile
+
+template <class Prob, int NS, int DMAX>
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    k_tc_gemm(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+              const unsigned char* __restrict__ slices, const int* __restrict__ expo, TcExtra x) {
+  using namespace tc;
+  constexpr int kA = NS * 2 * kAChunk, kB = NS * kBChunk, kStage = kA + kB;
+  constexpr int kAcc = DMAX + 1;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accf[kAcc], bar_accr[kAcc], bar_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  const int b = b0 + blockIdx.y;
+  const BoxDesc& d = L.desc[b];
+  const BoxRun rr = L.run[b];
+  int m, n, k;
+  if (!Prob::dims(L, d, rr, m, n, k)) return;
+  const int tms = (m + kRows - 1) / kRows, tns = (n + kCols - 1) / kCols;
+  if ((int)blockIdx.x >= tms * tns) return;
+  const int tm = blockIdx.x % tms, tn = blockIdx.x / tms;
+  const int i0 = tm * kRows, j0 = tn * kCols;
+  if (Prob::kUpper && j0 + kCols - 1 < i0) return;   // entirely below the diagonal
+  const int KS = (k + 15) / 16;
+  const TcBoxHost t = tb[blockIdx.y];
+  unsigned char* sm =
+      reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) { mbar_init(&bar_full[s], 1); mbar_init(&bar_empty[s], 1); }
+    for (int a = 0; a < kAcc; ++a) { mbar_init(&bar_accf[a], 1); mbar_init(&bar_accr[a], 8); }
+    mbar_init(&bar_done, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&s_tmem)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---- producer: two-stage bulk-copy pipeline
+    if (lane == 0) {
+      const unsigned char* srcA = slices + t.a_off + (int64_t)tm * KS * kA;
+      const unsigned char* srcB = slices + t.b_off + (int64_t)tn * KS * kB;
+      int issued = 0;
+      for (int ks = 0; ks < KS; ++ks) {
+        const int s = ks & 1;
+        if (ks >= 2 && !mbar_wait(&bar_empty[s], ((ks >> 1) - 1) & 1, abort_flag)) break;
+        unsigned char* st = sm + s * kStage;
+        mbar_expect_tx(&bar_full[s], (uint32_t)kStage);
+        bulk_g2s(st, srcA + (int64_t)ks * kA, (uint32_t)kA, &bar_full[s]);
+        bulk_g2s(st + kA, srcB + (int64_t)ks * kB, (uint32_t)kB, &bar_full[s]);
+        issued = ks + 1;
+      }
+      if (*abort_flag) {
+        // let the copies in flight land before the CTA's shared memory goes away
+        for (int ks = issued > 2 ? issued - 2 : 0; ks < issued; ++ks) {
+          const int s = ks & 1;
+          for (long long i = 0; i < kWaitLimit; ++i)
+            if (mbar_try(&bar_full[s], (ks >> 1) & 1)) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t smem0 = su32(sm);
+      const uint32_t boffA = Prob::kConj ? 0u : 512u;   // B rows for the A_re product
+      const uint32_t boffB = Prob::kConj ? 512u : 0u;   // B rows for the A_im product
+      const uint64_t dA = sdesc(0, 2048, 128), dB = sdesc(0, 1536, 128);
+      int nwin[kAcc];
+#pragma unroll
+      for (int a = 0; a < kAcc; ++a) nwin[a] = 0;
+      bool ok = true;
+      for (int ks = 0; ks < KS && ok; ++ks) {
+        const int s = ks & 1;
+        if (!mbar_wait(&bar_full[s], (ks >> 1) & 1, abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint32_t aS = smem0 + s * kStage, bS = aS + kA;
+#pragma unroll
+        for (int dd = 0; dd < kAcc; ++dd) {
+          const int W = window(dd, NS);
+          const bool start = ks % W == 0;
+          if (start && ks > 0) {
+            if (!mbar_wait(&bar_accr[dd], (nwin[dd] - 1) & 1, abort_flag)) { ok = false; break; }
+            fence_after();
+          }
+          if (start) ++nwin[dd];
+          const uint32_t dt = tmem + 64 * dd;
+          uint32_t acc = start ? 0u : 1u;
+          for (int p = plo(dd, NS); p <= phi(dd, NS); ++p) {
+            const int q = dd - p;
+            const uint32_t ar = aS + (2 * p) * kAChunk, ai = ar + kAChunk;
+            const uint32_t bq = bS + q * kBChunk;
+            mma(dt, dA + (ar >> 4), dB + ((bq + boffA) >> 4), acc);
+            mma(dt, dA + (ai >> 4), dB + ((bq + boffB) >> 4), 1u);
+            acc = 1u;
+          }
+          if ((ks + 1) % W == 0 || ks == KS - 1) commit(&bar_accf[dd]);
+        }
+        if (!ok) break;
+        commit(&bar_empty[s]);
+      }
+      // all MMAs issued by this thread complete before tensor memory is freed
+      commit(&bar_done);
+      for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try(&bar_done, 0)) break;
+    }
+  } else {
+    // ---- epilogue: drain each accumulator window into 64-bit integers
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int row = 32 * quarter + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
+    long long xh[16][2], xl[16][2];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) xh[c][0] = xh[c][1] = xl[c][0] = xl[c][1] = 0;
+    int nwin[kAcc];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a) nwin[a] = 0;
+    bool ok = true;
+    for (int ks = 0; ks < KS && ok; ++ks) {
+#pragma unroll
+      for (int dd = 0; dd < kAcc; ++dd) {
+        const int W = window(dd, NS);
+        if (!((ks + 1) % W == 0 || ks == KS - 1)) continue;
+        if (!mbar_wait(&bar_accf[dd], nwin[dd] & 1, abort_flag)) { ok = false; break; }
+        ++nwin[dd];
+        fence_after();
+        float vr[16], vi[16];
+        tmem_ld16(tl + 64 * dd + 16 * half, vr);
+        tmem_ld16(tl + 64 * dd + 32 + 16 * half, vi);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_accr[dd]);
+        const bool hi = dd <= 2;
+        const int sh = hi ? 8 * (2 - dd) : 8 * (DMAX - dd);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long r0 = (long long)__float2int_rn(vr[c]) << sh;
+          const long long r1 = (long long)__float2int_rn(vi[c]) << sh;
+          if (hi) { xh[c][0] += r0; xh[c][1] += r1; }
+          else { xl[c][0] += r0; xl[c][1] += r1; }
+        }
+      }
+    }
+    if (ok && !*abort_flag) {
+      const int i = i0 + row;
+      if (i < m) {
+        const int ei = expo[t.ea_off + i];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = j0 + 16 * half + c;
+          if (j >= n) continue;
+          const int E = ei + expo[t.eb_off + j];
+          const double vr = ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
+          const double vi = ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
+          Prob::epi(L, d, rr, x, i, j, vr, vi);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort_flag && tid == 0) set_status(L.status, kStatusTimeout);
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+size_t tc_smem_bytes(int ns) {
+  // at least 120 KB so that one CTA (holding all 512 tensor-memory columns)
+  // runs per SM
+  return std::max<size_t>((size_t)2 * (ns * 2 * tc::kAChunk + ns * tc::kBChunk) + 1024,
+                          (size_t)120 * 1024);
+}
+
+void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_t& expo_off,
+                 TcBoxHost& out) {
+  const int64_t ks = (k + 15) / 16;
+  const int64_t mb = (mrows + tc::kRows - 1) / tc::kRows, nb = (ncols + tc::kCols - 1) / tc::kCols;
+  out.a_off = slice_off;
+  slice_off += mb * ks * ns * 2 * tc::kAChunk;
+  out.b_off = slice_off;
+  slice_off += nb * ks * ns * tc::kBChunk;
+  out.ea_off = expo_off;
+  expo_off += mb * tc::kRows;
+  out.eb_off = expo_off;
+  expo_off += nb * tc::kCols;
+}
+
+template <class Prob, int NS, int DMAX>
+static void launch_tc(const char* name, const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb,
+                      void* slices, int* expo, int mmax, int nmax, const TcExtra& x, cudaStream_t st) {
+  if (nb <= 0) return;
+  unsigned char* sl = reinterpret_cast<unsigned char*>(slices);
+  const int big = std::max((mmax + tc::kRows - 1) / tc::kRows * tc::kRows,
+                           (nmax + tc::kCols - 1) / tc::kCols * tc::kCols);
+  dim3 gs((unsigned)((big + 7) / 8), 2, nb);
+  FMMLU_LAUNCH("tc_split", st, (k_tc_split<Prob, NS><<<gs, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
+  const size_t smem = tc_smem_bytes(NS);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_gemm<Prob, NS, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  const int tiles = ((mmax + tc::kRows - 1) / tc::kRows) * ((nmax + tc::kCols - 1) / tc::kCols);
+  dim3 gm((unsigned)tiles, nb);
+  FMMLU_LAUNCH(name, st,
+               (k_tc_gemm<Prob, NS, DMAX><<<gm, tc::kThreads, smem, st>>>(L, b0, d_tb, sl, expo, x)));
+}
+
+// which: 0 = G1 update, 1 = G3 update, 2 = W, 3 = Schur update
+void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
+                    int* expo, int amax, int nmax_max, int which, cudaStream_t st) {
+  const TcExtra x{nullptr, nullptr};
+  const int an = amax + nmax_max;
+  if (which == 0) launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, nb, d_tb, slices, expo, amax, an, x, st);
+  if (which == 1) launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, nb, d_tb, slices, expo, an, amax, x, st);
+  if (which == 2) launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, nb, d_tb, slices, expo, an, amax, x, st);
+  if (which == 3) launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, nb, d_tb, slices, expo, an, an, x, st);
+}
+
+void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
+                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, bool fp32,
+                    cudaStream_t st) {
+  const TcExtra x{d_gb, gbuf};
+  if (fp32)
+    launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, x, st);
+  else
+    launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, x, st);
+}
+
+}  // namespace fmmlu

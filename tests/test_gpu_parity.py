@@ -151,11 +151,12 @@ def test_eps_to_zero_is_dense_lu(pkg, ell):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
 
 
-@pytest.mark.parametrize("emul", [0, 1])
+@pytest.mark.parametrize("emul", [0, 1, 2])
 def test_schur_emulation_exact_limit_and_accuracy(pkg, ell, emul):
-    """Schur products in fp64 FMA (0) or on bf16 tensor cores by exact operand
-    splitting (1): eps -> 0 must still be the dense LU, eps = 1e-6 within 10 eps,
-    and both modes must agree far below eps."""
+    """Elimination products in fp64 FMA (0), or on the bf16 tensor cores by
+    exact operand splitting through tcgen05 with tensor-memory accumulators (1)
+    or through mma.sync (2): eps -> 0 must still be the dense LU, eps = 1e-6
+    within 10 eps, and every mode must agree with fp64 FMA far below eps."""
     s, A, b, xd = ell
     fac = _gpu_factor(pkg, s, K, 1e-14, leaf_size=24, precision=pkg.PRECISION_FP64,
                       schur_emulation=emul)
@@ -163,13 +164,13 @@ def test_schur_emulation_exact_limit_and_accuracy(pkg, ell, emul):
     fac.free()
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
     xs = {}
-    for mode in (0, 1):
+    for mode in sorted({0, emul}):
         fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
                           schur_emulation=mode)
         xs[mode] = fac.solve(torch.from_numpy(b)).cpu().numpy()
         fac.free()
     assert np.linalg.norm(A @ xs[emul] - b) / np.linalg.norm(b) <= 1e-5
-    assert np.linalg.norm(xs[0] - xs[1]) / np.linalg.norm(xs[0]) <= 1e-7
+    assert np.linalg.norm(xs[0] - xs[emul]) / np.linalg.norm(xs[0]) <= 1e-7
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
