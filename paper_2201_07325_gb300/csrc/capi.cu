@@ -685,7 +685,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (gram_col[sgi]) {
         if (gram_tc)
           launch_tc_gram(LD, b0, cnt, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g, amax,
-                         H->fp32, st);
+                         mmax, H->fp32, st);
         else
           launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
         CK(cudaGetLastError());
@@ -700,7 +700,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
       }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
-      const int kskip = use_oz ? kOzInnerMin : 0;
+      const int kskip = use_tc ? kTcInnerMin : use_oz ? kOzInnerMin : 0;
       launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
       launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc) {
@@ -710,7 +710,9 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 0, st);
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 1, st);
       }
-      launch_gemm_xrr(LD, b0, cnt, amax, st);
+      launch_gemm_xrr(LD, b0, cnt, amax, st, use_tc ? kTcInnerMin : 0);
+      if (use_tc)
+        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 4, st);
       if (gplan[sgi].dist) {
         CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
         CK(launch_gj_dist(LD, d_parts + gplan[sgi].pbeg, gplan[sgi].np, d_gj_scratch, amax, st));
@@ -749,7 +751,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           const double kt = std::ceil(m / 16.0) * 16.0;
           double pc = 4.0 * s_ * s_ * r_;
           for (int j = 0; j < rr.s; ++j) pc += 8.0 * j * (a - j - 1);
-          H->prof.add_work(gram_tc ? "tc_split" : "gram_split", 0, m * a * csz + ns * 4.0 * apad * kt);
+          H->prof.add_work(gram_tc ? "tc_split" : "gram_split", 0,
+                           gram_tc ? a * m * (4.0 * csz + 10.0 * ns) : m * a * csz + ns * 4.0 * apad * kt);
           // bf16 tensor flops of the upper-triangle tiles: digit pairs x 4 real
           // products x 2 flops x m x a (a + 1) / 2
           const double pairs = H->fp32 ? 13.0 : 28.0;
@@ -767,22 +770,31 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         // complex products: 8 fp64 flops per multiply-add on the FMA path; on
         // the tensor-core path (inner dimension >= kOzInnerMin) 28 digit pairs
         // x 4 real bf16 products x 2 flops, and the digit split of the operands
-        const bool tc_s = use_oz && rr.s >= kOzInnerMin, tc_r = use_oz && rr.r >= kOzInnerMin;
-        const double c_tc = 28.0 * 4.0 * 2.0, split_b = 16.0 + 28.0;   // split: read fp64, write digits
+        const int inner_min = use_tc ? kTcInnerMin : kOzInnerMin;
+        const bool tc_s = use_oz && rr.s >= inner_min, tc_r = use_oz && rr.r >= inner_min;
+        const double c_tc = 28.0 * 4.0 * 2.0;
+        // split bytes per element: the operand read twice (exponent, digits), 7 digits written
+        // as 2 (A side) or 3 (B side) bf16 parts
+        auto split = [](double ra, double rb, double kk) {
+          return ra * kk * (32.0 + 28.0) + rb * kk * (32.0 + 42.0);
+        };
         H->prof.add_work(tc_s ? "gemm_g1_tc" : "gemm_g1", (tc_s ? c_tc : 8.0) * r_ * (a + n_) * s_,
                          16.0 * (s_ * r_ + 2 * a * (a + n_)));
         H->prof.add_work(tc_s ? "gemm_g3_tc" : "gemm_g3", (tc_s ? c_tc : 8.0) * (a + n_) * r_ * s_,
                          16.0 * (s_ * r_ + 2 * a * (a + n_)));
         const char* split_name = use_tc ? "tc_split" : "oz_split";
-        if (tc_s) H->prof.add_work(split_name, 0, 2.0 * split_b * (r_ * s_ + s_ * (a + n_)));
-        H->prof.add_work("gemm_xrr", 8.0 * r_ * r_ * s_, 16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
+        if (tc_s) H->prof.add_work(split_name, 0, split(r_, a + n_, s_) + split(a + n_, r_, s_));
+        H->prof.add_work(use_tc && tc_s ? "gemm_xrr_tc" : "gemm_xrr",
+                         (use_tc && tc_s ? c_tc : 8.0) * r_ * r_ * s_,
+                         16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
+        if (use_tc && tc_s) H->prof.add_work(split_name, 0, split(r_, r_, s_));
         H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
         H->prof.add_work(tc_r ? "gemm_w_tc" : "gemm_w", (tc_r ? c_tc : 8.0) * (s_ + n_) * r_ * r_,
                          16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
         H->prof.add_work(tc_r ? "schur_tc" : "schur_update",
                          (tc_r ? c_tc : 8.0) * (s_ + n_) * (s_ + n_) * r_,
                          16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));
-        if (tc_r) H->prof.add_work(split_name, 0, split_b * (2 * (s_ + n_) * r_ + 2 * r_ * r_));
+        if (tc_r) H->prof.add_work(split_name, 0, split(s_ + n_, r_, r_) + split(s_ + n_, s_ + n_, r_));
       }
     }
     // solve plan for this level

@@ -186,7 +186,8 @@ void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, v
 // which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}
 void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
                           int* expo, int amax, int nmax_max, int which, cudaStream_t st);
-constexpr int kOzInnerMin = 32;   // inner dimension from which the tensor-core path is used
+constexpr int kOzInnerMin = 32;   // inner dimension from which the mma.sync path is used
+constexpr int kTcInnerMin = 16;   // inner dimension from which the tcgen05 path is used
 // Gram form of the ID (ozaki.cu, pchol.cu): G = M^H M of the ID matrix on the
 // tensor cores, then greedy pivoted Cholesky of G -- the same column selection
 // and the same R (up to row phases) as CPQR of M in exact arithmetic.
@@ -215,12 +216,13 @@ struct TcBoxHost {       // per box of a colour, planned from bounds
 void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_t& expo_off,
                  TcBoxHost& out);
 size_t tc_smem_bytes(int ns);
-// which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}, 3 = Schur update
+// which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}, 3 = Schur update,
+// 4 = X_RR = A_RR - A_RS T
 void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
                     int* expo, int amax, int nmax_max, int which, cudaStream_t st);
 void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, bool fp32,
-                    cudaStream_t st);
+                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, int mmax,
+                    bool fp32, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);
@@ -231,7 +233,7 @@ void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st, int kskip = 0);
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st, int kskip = 0);
-void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
+void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st, int kskip = 0);
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
 void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                    cudaStream_t st, int kskip = 0);

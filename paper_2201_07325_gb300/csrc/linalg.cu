@@ -494,12 +494,12 @@ struct EpiDiff {   // C = Y - acc
   __device__ void operator()(int i, int j, double2 v) { C[i + j * ldc] = csub(Y[i + j * ldy], v); }
 };
 
-__global__ void __launch_bounds__(256) k_gemm_xrr(LevelDev L, int b0) {
+__global__ void __launch_bounds__(256) k_gemm_xrr(LevelDev L, int b0, int kskip) {
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int a = d.a, s = run.s, r = run.r, n = run.n;
-  if (r == 0) return;
+  if (r == 0 || (kskip > 0 && s >= kskip)) return;
   int tm, tn;
   if (!tile_of(r, r, tm, tn)) return;
   const double2* G1 = L.arena + d.G1_off;
@@ -518,9 +518,10 @@ __global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0) {
   gauss_jordan(L.arena + d.Xinv_off, r, d.a, ipiv, L.status);
 }
 
-void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
+void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st, int kskip) {
   if (nb <= 0) return;
-  FMMLU_LAUNCH("gemm_xrr", st, k_gemm_xrr<<<dim3(tiles(amax, amax), nb), 256, 0, st>>>(L, b0));
+  FMMLU_LAUNCH("gemm_xrr", st,
+               k_gemm_xrr<<<dim3(tiles(amax, amax), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
 void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {

@@ -166,11 +166,12 @@ struct TcExtra {
   double2* gbuf;
 };
 
+// kAk / kBk: consecutive k of one row of A / column of B are contiguous in memory
 struct TcSchur {    // Delta(S|N, S|N) -= W X_RC: (s+n) x (s+n) x r
-  static constexpr bool kConj = false, kUpper = false;
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
   __device__ static bool dims(const LevelDev&, const BoxDesc&, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = rr.s + rr.n; n = m; k = rr.r; return rr.r >= kOzInnerMin;
+    m = rr.s + rr.n; n = m; k = rr.r; return rr.r >= kTcInnerMin;
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
     return L.Wbuf[d.W_off + i + (int64_t)kk * (d.a + d.nmax)];
@@ -198,10 +199,10 @@ struct TcSchur {    // Delta(S|N, S|N) -= W X_RC: (s+n) x (s+n) x r
 };
 
 struct TcW {        // W = X_CR X_RR^{-1}: (s+n) x r x r, stored
-  static constexpr bool kConj = false, kUpper = false;
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
   __device__ static bool dims(const LevelDev&, const BoxDesc&, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = rr.s + rr.n; n = rr.r; k = rr.r; return rr.r >= kOzInnerMin;
+    m = rr.s + rr.n; n = rr.r; k = rr.r; return rr.r >= kTcInnerMin;
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int kk) {
     return L.arena[d.G3_off + i + (int64_t)(rr.s + kk) * (d.a + d.nmax)];
@@ -216,10 +217,10 @@ struct TcW {        // W = X_CR X_RR^{-1}: (s+n) x r x r, stored
 };
 
 struct TcG1 {       // G1[s:a, :] -= T^T G1[0:s, :]: r x (a+n) x s
-  static constexpr bool kConj = false, kUpper = false;
+  static constexpr bool kConj = false, kUpper = false, kAk = true, kBk = true;
   __device__ static bool dims(const LevelDev&, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = rr.r; n = d.a + rr.n; k = rr.s; return rr.r > 0 && rr.s >= kOzInnerMin;
+    m = rr.r; n = d.a + rr.n; k = rr.s; return rr.r > 0 && rr.s >= kTcInnerMin;
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
     return L.arena[d.T_off + kk + (int64_t)i * d.a];
@@ -236,10 +237,10 @@ struct TcG1 {       // G1[s:a, :] -= T^T G1[0:s, :]: r x (a+n) x s
 };
 
 struct TcG3 {       // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
-  static constexpr bool kConj = false, kUpper = false;
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
   __device__ static bool dims(const LevelDev&, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = d.a + rr.n; n = rr.r; k = rr.s; return rr.r > 0 && rr.s >= kOzInnerMin;
+    m = d.a + rr.n; n = rr.r; k = rr.s; return rr.r > 0 && rr.s >= kTcInnerMin;
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
     return L.arena[d.G3_off + i + (int64_t)kk * (d.a + d.nmax)];
@@ -255,10 +256,29 @@ struct TcG3 {       // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
   }
 };
 
+struct TcXrr {      // X_RR = A_RR - A_RS T (before inversion): r x r x s
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
+  __device__ static bool dims(const LevelDev&, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.r; n = rr.r; k = rr.s; return rr.r > 0 && rr.s >= kTcInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i, int kk) {
+    return L.arena[d.G1_off + rr.s + i + (int64_t)kk * d.a];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.T_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const double2 y = L.arena[d.G1_off + rr.s + i + (int64_t)(rr.s + rr.n + j) * d.a];
+    L.arena[d.Xinv_off + i + (int64_t)j * d.a] = make_double2(y.x - vr, y.y - vi);
+  }
+};
+
 // G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
 template <typename CM>
 struct TcGram {
-  static constexpr bool kConj = true, kUpper = true;
+  static constexpr bool kConj = true, kUpper = true, kAk = true, kBk = true;
   __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int& m,
                               int& n, int& k) {
     m = d.a; n = d.a; k = 2 * rr.nq + 2 * L.n_proxy; return d.a > 0;
@@ -281,77 +301,147 @@ struct TcGram {
 };
 
 // ---------------------------------------------------------------------------
-// split kernels: one warp per row of A (side 0) or column of B (side 1)
+// split: (1) the power-of-two exponent of every row of A (side 0) / column of
+// B (side 1); (2) the digits, each thread converting 8 consecutive k of one
+// row into one 16-byte vector per digit and part (32 lanes = 32 consecutive
+// rows = 512 contiguous bytes of the core-matrix layout)
 
-template <class Prob, int NS>
-__global__ void __launch_bounds__(256) k_tc_split(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-                                                  unsigned char* slices, int* expo) {
+template <class Prob>
+__device__ __forceinline__ double2 tc_elem(const LevelDev& L, const BoxDesc& d, const BoxRun& rr,
+                                           bool side_b, int row, int kk) {
+  return side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
+}
+
+__device__ __forceinline__ int tc_exponent(double mx) {
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);   // mx < 2^e
+    e += 1;          // |v| < 2^(e-1): the leading balanced digit stays in [-128, 128]
+  }
+  return e;
+}
+
+template <class Prob, bool SideB>
+__global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+                                                int* expo) {
   const int b = b0 + blockIdx.z;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
   int m, n, k;
   if (!Prob::dims(L, d, rr, m, n, k)) return;
   const TcBoxHost t = tb[blockIdx.z];
-  const bool side_b = blockIdx.y == 1;
+  constexpr bool side_b = SideB;
+  constexpr bool kcontig = SideB ? Prob::kBk : Prob::kAk;
   const int len = side_b ? n : m;
   const int lpad = side_b ? (n + tc::kCols - 1) / tc::kCols * tc::kCols
                           : (m + tc::kRows - 1) / tc::kRows * tc::kRows;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + warp;
-  if (row >= lpad) return;
-  const int KS = (k + 15) / 16;
-  double mx = 0.0;
-  if (row < len)
-    for (int kk = lane; kk < k; kk += 32) {
-      const double2 v = side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const bool bad = !(mx <= 1.7976931348623157e308);
-  if (bad) {
-    if (lane == 0) set_status(L.status, kStatusNonfinite);
-    mx = 0.0;
-  }
-  int e = 0;
-  if (mx > 0.0) {
-    frexp(mx, &e);   // mx < 2^e
-    e += 1;          // |v| < 2^(e-1): the leading balanced digit stays in [-128, 128]
-  }
-  if (lane == 0) expo[(side_b ? t.eb_off : t.ea_off) + row] = e;
-  unsigned char* base = slices + (side_b ? t.b_off : t.a_off);
-  const int blk = side_b ? row / tc::kCols : row / tc::kRows;
-  const int r = side_b ? row % tc::kCols : row % tc::kRows;
-  for (int kk = lane; kk < KS * 16; kk += 32) {
-    double2 v = make_double2(0.0, 0.0);
-    if (row < len && kk < k && !bad)
-      v = side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
-    int cr[NS], ci[NS];
-    tc::balanced_digits<NS>(v.x, e, cr);
-    tc::balanced_digits<NS>(v.y, e, ci);
-    const int ks = kk >> 4, kq = kk & 15;
-    if (!side_b) {
-      unsigned char* step = base + ((int64_t)blk * KS + ks) * (2 * NS) * tc::kAChunk;
-      const int off = tc::canon16(r, kq, tc::kRows);
-#pragma unroll
-      for (int p = 0; p < NS; ++p) {
-        *reinterpret_cast<__nv_bfloat16*>(step + (2 * p) * tc::kAChunk + off) = __int2bfloat16_rn(cr[p]);
-        *reinterpret_cast<__nv_bfloat16*>(step + (2 * p + 1) * tc::kAChunk + off) =
-            __int2bfloat16_rn(ci[p]);
+  int* ex = expo + (side_b ? t.eb_off : t.ea_off);
+  const int lane = threadIdx.x & 31;
+  if (kcontig) {                 // a warp per row, lanes along k
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= lpad) return;
+    double mx = 0.0;
+    if (row < len)
+      for (int kk = lane; kk < k; kk += 32) {
+        const double2 v = tc_elem<Prob>(L, d, rr, side_b, row, kk);
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
       }
-    } else {
-      unsigned char* step = base + ((int64_t)blk * KS + ks) * NS * tc::kBChunk;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (!(mx <= 1.7976931348623157e308)) {
+      if (lane == 0) set_status(L.status, kStatusNonfinite);
+      mx = 0.0;
+    }
+    if (lane == 0) ex[row] = tc_exponent(mx);
+  } else {                       // a thread per row, consecutive rows contiguous
+    const int row = blockIdx.x * 256 + threadIdx.x;
+    if (blockIdx.x * 256 >= lpad) return;
+    if (row >= lpad) return;
+    double mx = 0.0;
+    if (row < len)
+      for (int kk = 0; kk < k; ++kk) {
+        const double2 v = tc_elem<Prob>(L, d, rr, side_b, row, kk);
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      }
+    if (!(mx <= 1.7976931348623157e308)) {
+      set_status(L.status, kStatusNonfinite);
+      mx = 0.0;
+    }
+    ex[row] = tc_exponent(mx);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
+  __nv_bfloat162 h = __halves2bfloat162(__int2bfloat16_rn(lo), __int2bfloat16_rn(hi));
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// grid: x = 32-row groups, y = k-octet groups of 8 (one per warp), z = boxes
+template <class Prob, int NS, bool SideB>
+__global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+                                                   unsigned char* slices, const int* __restrict__ expo) {
+  const int b = b0 + blockIdx.z;
+  const BoxDesc& d = L.desc[b];
+  const BoxRun rr = L.run[b];
+  int m, n, k;
+  if (!Prob::dims(L, d, rr, m, n, k)) return;
+  const TcBoxHost t = tb[blockIdx.z];
+  const int len = SideB ? n : m;
+  const int lpad = SideB ? (n + tc::kCols - 1) / tc::kCols * tc::kCols
+                         : (m + tc::kRows - 1) / tc::kRows * tc::kRows;
+  const int KS = (k + 15) / 16;
+  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int ko = blockIdx.y * 8 + (threadIdx.x >> 5);      // k-octet
+  if (blockIdx.x * 32 >= lpad || ko >= 2 * KS) return;
+  if (row >= lpad) return;
+  const int e = expo[(SideB ? t.eb_off : t.ea_off) + row];
+  int cr[8][NS], ci[8][NS];
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        unsigned char* dg = step + q * tc::kBChunk;
-        // three 32-row parts: [-im | re | im], or [re | im | -re] for conj(A)
-        const int p0 = Prob::kConj ? cr[q] : -ci[q];
-        const int p1 = Prob::kConj ? ci[q] : cr[q];
-        const int p2 = Prob::kConj ? -cr[q] : ci[q];
-        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r, kq, 3 * tc::kCols)) = __int2bfloat16_rn(p0);
-        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r + tc::kCols, kq, 3 * tc::kCols)) =
-            __int2bfloat16_rn(p1);
-        *reinterpret_cast<__nv_bfloat16*>(dg + tc::canon16(r + 2 * tc::kCols, kq, 3 * tc::kCols)) =
-            __int2bfloat16_rn(p2);
+  for (int u = 0; u < 8; ++u) {
+    const int kk = 8 * ko + u;
+    double2 v = make_double2(0.0, 0.0);
+    if (row < len && kk < k) v = tc_elem<Prob>(L, d, rr, SideB, row, kk);
+    if (!(fabs(v.x) <= 1.7976931348623157e308 && fabs(v.y) <= 1.7976931348623157e308))
+      v = make_double2(0.0, 0.0);   // reported by the exponent pass
+    tc::balanced_digits<NS>(v.x, e, cr[u]);
+    tc::balanced_digits<NS>(v.y, e, ci[u]);
+  }
+  const int ks = ko >> 1, kc = ko & 1;
+  if (!SideB) {
+    const int blk = row / tc::kRows, r = row % tc::kRows;
+    unsigned char* step = slices + t.a_off + ((int64_t)blk * KS + ks) * (2 * NS) * tc::kAChunk;
+    const int off = (kc * (tc::kRows / 8) + (r >> 3)) * 128 + (r & 7) * 16;
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      uint4 vr, vi;
+      vr.x = pack_bf16x2(cr[0][p], cr[1][p]); vr.y = pack_bf16x2(cr[2][p], cr[3][p]);
+      vr.z = pack_bf16x2(cr[4][p], cr[5][p]); vr.w = pack_bf16x2(cr[6][p], cr[7][p]);
+      vi.x = pack_bf16x2(ci[0][p], ci[1][p]); vi.y = pack_bf16x2(ci[2][p], ci[3][p]);
+      vi.z = pack_bf16x2(ci[4][p], ci[5][p]); vi.w = pack_bf16x2(ci[6][p], ci[7][p]);
+      *reinterpret_cast<uint4*>(step + (2 * p) * tc::kAChunk + off) = vr;
+      *reinterpret_cast<uint4*>(step + (2 * p + 1) * tc::kAChunk + off) = vi;
+    }
+  } else {
+    const int blk = row / tc::kCols, r = row % tc::kCols;
+    unsigned char* step = slices + t.b_off + ((int64_t)blk * KS + ks) * NS * tc::kBChunk;
+    constexpr int rg = 3 * tc::kCols / 8;   // row groups of the three-part block
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      unsigned char* dg = step + q * tc::kBChunk;
+      // three 32-row parts: [-im | re | im], or [re | im | -re] for conj(A)
+#pragma unroll
+      for (int part = 0; part < 3; ++part) {
+        int w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int re = cr[u][q], im = ci[u][q];
+          w[u] = Prob::kConj ? (part == 0 ? re : part == 1 ? im : -re)
+                             : (part == 0 ? -im : part == 1 ? re : im);
+        }
+        uint4 v;
+        v.x = pack_bf16x2(w[0], w[1]); v.y = pack_bf16x2(w[2], w[3]);
+        v.z = pack_bf16x2(w[4], w[5]); v.w = pack_bf16x2(w[6], w[7]);
+        const int pr = part * tc::kCols + r;
+        *reinterpret_cast<uint4*>(dg + (kc * rg + (pr >> 3)) * 128 + (pr & 7) * 16) = v;
       }
     }
   }
@@ -563,13 +653,24 @@ void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_
 
 template <class Prob, int NS, int DMAX>
 static void launch_tc(const char* name, const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb,
-                      void* slices, int* expo, int mmax, int nmax, const TcExtra& x, cudaStream_t st) {
+                      void* slices, int* expo, int mmax, int nmax, int kmax, const TcExtra& x,
+                      cudaStream_t st) {
   if (nb <= 0) return;
   unsigned char* sl = reinterpret_cast<unsigned char*>(slices);
-  const int big = std::max((mmax + tc::kRows - 1) / tc::kRows * tc::kRows,
-                           (nmax + tc::kCols - 1) / tc::kCols * tc::kCols);
-  dim3 gs((unsigned)((big + 7) / 8), 2, nb);
-  FMMLU_LAUNCH("tc_split", st, (k_tc_split<Prob, NS><<<gs, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
+  // exponents: a warp per row where k is contiguous, else a thread per row
+  const int pa = (mmax + tc::kRows - 1) / tc::kRows * tc::kRows;
+  const int pb = (nmax + tc::kCols - 1) / tc::kCols * tc::kCols;
+  dim3 gea((unsigned)(Prob::kAk ? (pa + 7) / 8 : (pa + 255) / 256), 1, nb);
+  dim3 geb((unsigned)(Prob::kBk ? (pb + 7) / 8 : (pb + 255) / 256), 1, nb);
+  FMMLU_LAUNCH("tc_split", st, (k_tc_exp<Prob, false><<<gea, 256, 0, st>>>(L, b0, d_tb, expo)));
+  FMMLU_LAUNCH("tc_split", st, (k_tc_exp<Prob, true><<<geb, 256, 0, st>>>(L, b0, d_tb, expo)));
+  dim3 gda((unsigned)((mmax + tc::kRows - 1) / tc::kRows * (tc::kRows / 32)),
+           (unsigned)((2 * ((kmax + 15) / 16) + 7) / 8), nb);
+  dim3 gdb((unsigned)((nmax + 31) / 32), (unsigned)((2 * ((kmax + 15) / 16) + 7) / 8), nb);
+  FMMLU_LAUNCH("tc_split", st,
+               (k_tc_digits<Prob, NS, false><<<gda, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
+  FMMLU_LAUNCH("tc_split", st,
+               (k_tc_digits<Prob, NS, true><<<gdb, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
   const size_t smem = tc_smem_bytes(NS);
   static bool attr = false;
   if (!attr) {
@@ -583,25 +684,32 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, int nb, const
                (k_tc_gemm<Prob, NS, DMAX><<<gm, tc::kThreads, smem, st>>>(L, b0, d_tb, sl, expo, x)));
 }
 
-// which: 0 = G1 update, 1 = G3 update, 2 = W, 3 = Schur update
+// which: 0 = G1 update, 1 = G3 update, 2 = W, 3 = Schur update, 4 = X_RR
 void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
                     int* expo, int amax, int nmax_max, int which, cudaStream_t st) {
   const TcExtra x{nullptr, nullptr};
   const int an = amax + nmax_max;
-  if (which == 0) launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, nb, d_tb, slices, expo, amax, an, x, st);
-  if (which == 1) launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, nb, d_tb, slices, expo, an, amax, x, st);
-  if (which == 2) launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, nb, d_tb, slices, expo, an, amax, x, st);
-  if (which == 3) launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, nb, d_tb, slices, expo, an, an, x, st);
+  if (which == 0)
+    launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, nb, d_tb, slices, expo, amax, an, amax, x, st);
+  if (which == 1)
+    launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, nb, d_tb, slices, expo, an, amax, amax, x, st);
+  if (which == 2)
+    launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, nb, d_tb, slices, expo, an, amax, amax, x, st);
+  if (which == 3)
+    launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, nb, d_tb, slices, expo, an, an, amax, x, st);
+  if (which == 4)
+    launch_tc<TcXrr, 7, 6>("gemm_xrr_tc", L, b0, nb, d_tb, slices, expo, amax, amax, amax, x, st);
 }
 
 void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, bool fp32,
-                    cudaStream_t st) {
+                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, int mmax,
+                    bool fp32, cudaStream_t st) {
   const TcExtra x{d_gb, gbuf};
   if (fp32)
-    launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, x, st);
+    launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, mmax, x, st);
   else
-    launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, x, st);
+    launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, mmax, x,
+                                     st);
 }
 
 }  // namespace fmmlu
