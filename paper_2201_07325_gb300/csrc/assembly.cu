@@ -93,104 +93,80 @@ void launch_gather_rows(const LevelDev& L, int b0, int nb, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 
-constexpr int kIdRows = 64;
+constexpr int kIdRows = 64;   // half-rows per block (pairs of rows)
 
+// The rows come in pairs that share a kernel evaluation: row i < nq (A(q_i, b_j),
+// outgoing ring) and row nq + i (A(b_j, q_i), incoming ring, the transpose
+// block); proxy row 2nq + l (K(y_l, b_j)) and 2nq + np + l (G(b_j, y_l)).
 template <typename C>
 __global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
+  using R = decltype(C().x);
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
-  int nq = L.run[b].nq;
-  int np = L.n_proxy;
-  int m = 2 * nq + 2 * np;
-  int row0 = blockIdx.x * kIdRows;
-  if (row0 >= m) return;
-  int a = d.a;
+  const int nq = L.run[b].nq;
+  const int np = L.n_proxy;
+  const int half = nq + np;
+  const int row0 = blockIdx.x * kIdRows;
+  if (row0 >= half) return;
+  const int a = d.a;
   const int* qdof = L.rows + d.rows_off;
   const int* qpos = qdof + d.qmax;
   const int* qloc = qpos + d.qmax;
   const int bbase = L.cur_off[d.cur];
   C* M = reinterpret_cast<C*>(L.Mbuf) + d.M_off;
-  double rho = L.proxy_factor * 0.86602540378443864676 * d.h;
-  double cg = sqrt(4.0 * kPi * rho * rho / np);
-  int rows = min(kIdRows, m - row0);
+  const double rho = L.proxy_factor * 0.86602540378443864676 * d.h;
+  const double cg = sqrt(4.0 * kPi * rho * rho / np);
+  const int rows = min(kIdRows, half - row0);
+  const R kk = (R)g.k, ee = (R)g.eta;
   for (int e = threadIdx.x; e < rows * a; e += blockDim.x) {
-    int i = row0 + e % rows;
-    int j = e / rows;
-    int jd = L.act_dof[bbase + j];
-    if (sizeof(C) == sizeof(float2)) {
-      // mixed path: complex64 kernel blocks (Schur updates rounded to fp32)
-      float2 v;
-      const float kf = (float)g.k, ef = (float)g.eta;
-      if (i < 2 * nq) {
-        const bool out = i < nq;
-        const int i2 = out ? i : i - nq;
-        const int q = qdof[i2];
-        const int t = out ? q : jd, sdof = out ? jd : q;
-        v = comb_kernel_f(g.px[t], g.py[t], g.pz[t], g.px[sdof], g.py[sdof], g.pz[sdof],
-                          (float)g.nx[sdof], (float)g.ny[sdof], (float)g.nz[sdof], kf, ef);
-        v = cscale(v, (float)(g.sw[q] * g.sw[jd]));
-        int64_t off = L.qpair[d.qpair + 2 * qloc[i2] + (out ? 0 : 1)];
-        if (off >= 0) {
-          double2 dv = out ? L.delta[off + qpos[i2] + (int64_t)j * L.cur_a0[L.qlist[d.qbeg + qloc[i2]]]]
-                           : L.delta[off + j + (int64_t)qpos[i2] * a];
-          v = cadd(v, make_float2((float)dv.x, (float)dv.y));
-        }
-      } else {
-        int l = i - 2 * nq;
-        bool incoming = l >= np;
-        if (incoming) l -= np;
-        double ux, uy, uz;
-        fib_point(l, np, ux, uy, uz);
-        double yx = d.cx + rho * ux, yy = d.cy + rho * uy, yz = d.cz + rho * uz;
-        if (!incoming)
-          v = comb_kernel_f(yx, yy, yz, g.px[jd], g.py[jd], g.pz[jd], (float)g.nx[jd],
-                            (float)g.ny[jd], (float)g.nz[jd], kf, ef);
-        else
-          v = green_f(g.px[jd], g.py[jd], g.pz[jd], yx, yy, yz, kf);
-        v = cscale(v, (float)(cg * g.sw[jd]));
-      }
-      reinterpret_cast<float2*>(M)[i + (int64_t)j * d.mmax] = v;
-      continue;
-    }
-    double2 v;
+    const int i = row0 + e % rows;
+    const int j = e / rows;
+    const int jd = L.act_dof[bbase + j];
+    C v_out, v_in;
+    int r_out, r_in;
     if (i < nq) {
-      int q = qdof[i];
-      v = entry(g, q, jd);
-      int64_t off = L.qpair[d.qpair + 2 * qloc[i]];
-      if (off >= 0) {
-        int ldc = L.cur_a0[L.qlist[d.qbeg + qloc[i]]];
-        v = cadd(v, L.delta[off + qpos[i] + (int64_t)j * ldc]);
+      const int q = qdof[i];
+      typename CT<R>::T kqb, kbq, gq;
+      // coordinate differences in fp64 (cancellation), the rest in R
+      comb_kernel_pair<R>((R)(g.px[jd] - g.px[q]), (R)(g.py[jd] - g.py[q]), (R)(g.pz[jd] - g.pz[q]),
+                          (R)g.nx[q], (R)g.ny[q], (R)g.nz[q], (R)g.nx[jd], (R)g.ny[jd],
+                          (R)g.nz[jd], kk, ee, kqb, kbq, gq);
+      const R sc = (R)(g.sw[q] * g.sw[jd]);
+      double2 o = to_d2(cscale(kqb, sc)), t = to_d2(cscale(kbq, sc));
+      const int64_t off_o = L.qpair[d.qpair + 2 * qloc[i]];
+      if (off_o >= 0) {
+        const int ldc = L.cur_a0[L.qlist[d.qbeg + qloc[i]]];
+        o = cadd(o, L.delta[off_o + qpos[i] + (int64_t)j * ldc]);
       }
-    } else if (i < 2 * nq) {
-      int i2 = i - nq;
-      int q = qdof[i2];
-      v = entry(g, jd, q);
-      int64_t off = L.qpair[d.qpair + 2 * qloc[i2] + 1];
-      if (off >= 0) v = cadd(v, L.delta[off + j + (int64_t)qpos[i2] * a]);
+      const int64_t off_i = L.qpair[d.qpair + 2 * qloc[i] + 1];
+      if (off_i >= 0) t = cadd(t, L.delta[off_i + j + (int64_t)qpos[i] * a]);
+      v_out = from_d2<C>(o);
+      v_in = from_d2<C>(t);
+      r_out = i;
+      r_in = nq + i;
     } else {
-      int l = i - 2 * nq;
-      bool incoming = l >= np;
-      if (incoming) l -= np;
+      const int l = i - nq;
       double ux, uy, uz;
       fib_point(l, np, ux, uy, uz);
-      double yx = d.cx + rho * ux, yy = d.cy + rho * uy, yz = d.cz + rho * uz;
-      double s = cg * g.sw[jd];
-      if (!incoming) {
-        v = comb_kernel(yx, yy, yz, g.px[jd], g.py[jd], g.pz[jd], g.nx[jd], g.ny[jd],
-                        g.nz[jd], g.k, g.eta);
-      } else {
-        v = green(g.px[jd], g.py[jd], g.pz[jd], yx, yy, yz, g.k);
-      }
-      v = cscale(v, s);
+      const double yx = d.cx + rho * ux, yy = d.cy + rho * uy, yz = d.cz + rho * uz;
+      typename CT<R>::T kyb, kby, gy;
+      comb_kernel_pair<R>((R)(g.px[jd] - yx), (R)(g.py[jd] - yy), (R)(g.pz[jd] - yz), R(0), R(0),
+                          R(0), (R)g.nx[jd], (R)g.ny[jd], (R)g.nz[jd], kk, ee, kyb, kby, gy);
+      const R sc = (R)(cg * g.sw[jd]);
+      v_out = from_d2<C>(to_d2(cscale(kyb, sc)));   // K(y_l, b_j): outgoing proxy row
+      v_in = from_d2<C>(to_d2(cscale(gy, sc)));     // G(b_j, y_l): incoming proxy row
+      r_out = 2 * nq + l;
+      r_in = 2 * nq + np + l;
     }
-    reinterpret_cast<double2*>(M)[i + (int64_t)j * d.mmax] = v;
+    M[r_out + (int64_t)j * d.mmax] = v_out;
+    M[r_in + (int64_t)j * d.mmax] = v_in;
   }
 }
 
 void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, int mmax_max,
                         bool fp32, cudaStream_t st) {
   if (nb <= 0) return;
-  dim3 grid((mmax_max + kIdRows - 1) / kIdRows, nb);
+  dim3 grid((mmax_max / 2 + kIdRows - 1) / kIdRows, nb);   // m = 2 (nq + np) rows, in pairs
   if (fp32)
     FMMLU_LAUNCH("assemble_id", st, k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0));
   else
@@ -209,65 +185,72 @@ __device__ __forceinline__ Idx bpiv(const LevelDev& L, const BoxDesc& d, const i
   return Idx{L.act_dof[L.cur_off[d.cur] + p], 0, p};
 }
 
-__device__ __forceinline__ double2 elem(const LevelDev& L, const Geometry& g, const BoxDesc& d,
-                                        Idx r, Idx c) {
-  double2 v = entry(g, r.dof, c.dof);
-  int cnt = 1 + d.ncnt;
-  int64_t off = L.pairtab[d.pairtab + (int64_t)r.loc * cnt + c.loc];
+// G1 = A[B_piv, (S|N|R)] (a x (a+n), ld a) and G3 = A[(S|N|R), B_piv]
+// ((a+n) x a, ld a+nmax): G3[j][i] is the transposed pair of G1[i][j], so one
+// kernel evaluation gives both. A block takes 32 x 32 pairs (i in B_piv, j in
+// [S|N|R]); G1 is written along i, G3 through a shared-memory transpose along j.
+constexpr int kElimT = 32;
+
+__device__ __forceinline__ Idx col_idx(const LevelDev& L, const BoxDesc& d, const int* perm,
+                                       const int* ndof, const int* npos, const int* nloc, int s,
+                                       int n, int j) {
+  return j < s ? bpiv(L, d, perm, j)
+               : (j < s + n ? Idx{ndof[j - s], nloc[j - s], npos[j - s]} : bpiv(L, d, perm, j - n));
+}
+
+__device__ __forceinline__ double2 add_delta(const LevelDev& L, const BoxDesc& d, double2 v, Idx r,
+                                             Idx c) {
+  const int cnt = 1 + d.ncnt;
+  const int64_t off = L.pairtab[d.pairtab + (int64_t)r.loc * cnt + c.loc];
   if (off >= 0) {
-    int ld = r.loc == 0 ? d.a : L.cur_a0[L.nlist[d.nbeg + r.loc - 1]];
+    const int ld = r.loc == 0 ? d.a : L.cur_a0[L.nlist[d.nbeg + r.loc - 1]];
     v = cadd(v, L.delta[off + r.pos + (int64_t)c.pos * ld]);
   }
   return v;
 }
 
-constexpr int kElimTile = 4096;
-
-__global__ void k_assemble_elim(LevelDev L, Geometry g, int b0) {
-  int b = b0 + blockIdx.z;
+__global__ void __launch_bounds__(256) k_assemble_elim(LevelDev L, Geometry g, int b0) {
+  __shared__ double2 t3[kElimT][kElimT + 1];
+  const int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
-  int a = d.a, s = run.s, n = run.n;
+  const int a = d.a, s = run.s, n = run.n;
   if (s >= a) return;   // nothing to eliminate
+  const int ti = (a + kElimT - 1) / kElimT, tj = (a + n + kElimT - 1) / kElimT;
+  if ((int)blockIdx.x >= ti * tj) return;
+  const int i0 = (blockIdx.x % ti) * kElimT, j0 = (blockIdx.x / ti) * kElimT;
   const int* perm = L.iarena + d.idx_off + d.a + d.nmax;
   const int* ndof = L.rows + d.rows_off + 3 * d.qmax;
   const int* npos = ndof + d.nmax;
   const int* nloc = npos + d.nmax;
-  int64_t total = (int64_t)a * (a + n);
-  int64_t e0 = (int64_t)blockIdx.x * kElimTile;
-  if (e0 >= total) return;
-  int64_t e1 = min(total, e0 + kElimTile);
-  bool first = blockIdx.y == 0;
   double2* G1 = L.arena + d.G1_off;
   double2* G3 = L.arena + d.G3_off;
-  int ld3 = a + d.nmax;
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    if (first) {
-      // G1: a x (a+n), rows B_piv, cols [S | N | R]
-      int i = (int)(e % a), j = (int)(e / a);
-      Idx r = bpiv(L, d, perm, i);
-      Idx c = j < s ? bpiv(L, d, perm, j)
-                    : (j < s + n ? Idx{ndof[j - s], nloc[j - s], npos[j - s]}
-                                 : bpiv(L, d, perm, j - n));
-      G1[i + (int64_t)j * a] = elem(L, g, d, r, c);
-    } else {
-      // G3: (a+n) x a, rows [S | N | R], cols B_piv
-      int rows = a + n;
-      int i = (int)(e % rows), j = (int)(e / rows);
-      Idx r = i < s ? bpiv(L, d, perm, i)
-                    : (i < s + n ? Idx{ndof[i - s], nloc[i - s], npos[i - s]}
-                                 : bpiv(L, d, perm, i - n));
-      Idx c = bpiv(L, d, perm, j);
-      G3[i + (int64_t)j * ld3] = elem(L, g, d, r, c);
+  const int ld3 = a + d.nmax;
+  const int li = threadIdx.x & 31;
+  for (int lj = threadIdx.x >> 5; lj < kElimT; lj += blockDim.x >> 5) {
+    const int i = i0 + li, j = j0 + lj;
+    if (i < a && j < a + n) {
+      const Idx r = bpiv(L, d, perm, i);
+      const Idx c = col_idx(L, d, perm, ndof, npos, nloc, s, n, j);
+      double2 arc, acr;
+      entry_pair(g, r.dof, c.dof, arc, acr);
+      G1[i + (int64_t)j * a] = add_delta(L, d, arc, r, c);
+      t3[lj][li] = add_delta(L, d, acr, c, r);
     }
+  }
+  __syncthreads();
+  const int lj = threadIdx.x & 31;
+  for (int lii = threadIdx.x >> 5; lii < kElimT; lii += blockDim.x >> 5) {
+    const int i = i0 + lii, j = j0 + lj;
+    if (i < a && j < a + n) G3[j + (int64_t)i * ld3] = t3[lj][lii];
   }
 }
 
 void launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb, int amax,
                           int nmax_max, cudaStream_t st) {
   if (nb <= 0) return;
-  int64_t total = (int64_t)amax * (amax + nmax_max);
-  dim3 grid((unsigned)((total + kElimTile - 1) / kElimTile), 2, nb);
+  const int ti = (amax + kElimT - 1) / kElimT, tj = (amax + nmax_max + kElimT - 1) / kElimT;
+  dim3 grid((unsigned)(ti * tj), nb);
   FMMLU_LAUNCH("assemble_elim", st, k_assemble_elim<<<grid, 256, 0, st>>>(L, g, b0));
 }
 

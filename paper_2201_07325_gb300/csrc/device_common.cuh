@@ -160,6 +160,42 @@ __device__ __forceinline__ double2 entry(const Geometry& g, int i, int j) {
   return cscale(kv, g.sw[i] * g.sw[j]);
 }
 
+// K(t, s) and K(s, t) of one pair from a single evaluation of G(t, s) = G(s, t):
+//   K(t, s) = G (i k r - 1) ((s - t).n(s)) / r^2 - i eta G
+//   K(s, t) = G (i k r - 1) ((t - s).n(t)) / r^2 - i eta G
+template <typename R>
+__device__ __forceinline__ void comb_kernel_pair(R dx, R dy, R dz,   // s - t
+                                                 R tnx, R tny, R tnz, R snx, R sny, R snz, R k,
+                                                 R eta, typename CT<R>::T& kts,
+                                                 typename CT<R>::T& kst, typename CT<R>::T& g) {
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  const R r = sqrt(r2);
+  R sn, cs;
+  sincos(k * r, &sn, &cs);
+  const R ginv = R(1) / (R(4 * kPi) * r);
+  g = mk(cs * ginv, sn * ginv);
+  const typename CT<R>::T gf = cmul(g, mk(R(-1), k * r));   // G (i k r - 1)
+  const R pts = (dx * snx + dy * sny + dz * snz) / r2;
+  const R pst = -(dx * tnx + dy * tny + dz * tnz) / r2;
+  kts = mk(gf.x * pts + eta * g.y, gf.y * pts - eta * g.x);
+  kst = mk(gf.x * pst + eta * g.y, gf.y * pst - eta * g.x);
+}
+
+// A(i, j) and A(j, i) of the scaled system (i != j), one kernel evaluation
+__device__ __forceinline__ void entry_pair(const Geometry& g, int i, int j, double2& aij,
+                                           double2& aji) {
+  if (i == j) {
+    aij = aji = entry(g, i, i);
+    return;
+  }
+  double2 kij, kji, gg;
+  comb_kernel_pair<double>(g.px[j] - g.px[i], g.py[j] - g.py[i], g.pz[j] - g.pz[i], g.nx[i],
+                           g.ny[i], g.nz[i], g.nx[j], g.ny[j], g.nz[j], g.k, g.eta, kij, kji, gg);
+  const double sc = g.sw[i] * g.sw[j];
+  aij = cscale(kij, sc);
+  aji = cscale(kji, sc);
+}
+
 // l-th of n Fibonacci points on the unit sphere
 __device__ __forceinline__ void fib_point(int l, int n, double& ux, double& uy,
                                           double& uz) {
