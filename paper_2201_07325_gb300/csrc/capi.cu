@@ -98,6 +98,50 @@ struct DevPool {
   ~DevPool() { release(); }
 };
 
+inline void cudaFreeHost_void(BoxRun* p) { if (p) cudaFreeHost(p); }
+
+// A unit list of tcgen05 launches: pinned host staging and its device copy.
+// The staging buffer is rewritten only after the previous copy out of it has
+// run (event); the device copy is stream-ordered after the launches that read
+// the previous list. Growing waits for the stream (the old buffers may still
+// be read).
+struct UnitBuf {
+  TcUnit* h = nullptr;
+  TcUnit* d = nullptr;
+  size_t cap = 0;
+  cudaEvent_t copied = nullptr;
+  bool pending = false;
+  void upload(const std::vector<TcUnit>& u, cudaStream_t st) {
+    if (u.empty()) return;
+    if (!copied) CK(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+    if (pending) CK(cudaEventSynchronize(copied));
+    pending = false;
+    if (u.size() > cap) {
+      CK(cudaStreamSynchronize(st));
+      release_buffers();
+      cap = std::max(u.size(), (size_t)4096);
+      CK(cudaMallocHost(&h, cap * sizeof(TcUnit)));
+      CK(cudaMalloc(&d, cap * sizeof(TcUnit)));
+    }
+    std::memcpy(h, u.data(), u.size() * sizeof(TcUnit));
+    CK(cudaMemcpyAsync(d, h, u.size() * sizeof(TcUnit), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(copied, st));
+    pending = true;
+  }
+  void release_buffers() {
+    if (h) cudaFreeHost(h);
+    if (d) cudaFree(d);
+    h = nullptr;
+    d = nullptr;
+    cap = 0;
+  }
+  ~UnitBuf() {
+    if (pending) cudaEventSynchronize(copied);
+    release_buffers();
+    if (copied) cudaEventDestroy(copied);
+  }
+};
+
 inline uint64_t pkey(int x, int y) { return ((uint64_t)(uint32_t)x << 32) | (uint32_t)y; }
 
 void default_opts(fmmlu_opts* o) {
@@ -329,6 +373,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
   Timer total_timer;
   DevPool work;   // freed at the end of the factorization
+  UnitBuf gram_units, elim_units;   // launch lists of the tcgen05 path
   H->d_perm = H->mem.get<int>((size_t)n);
   CK(cudaMemcpyAsync(H->d_perm, tree->d_perm, n * sizeof(int), cudaMemcpyDeviceToDevice, st));
   double* soa = work.get<double>((size_t)n * 8);
@@ -449,6 +494,12 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     LevelDev LD;
     LD.desc = lw.up(desc, st);
     BoxRun* d_run = lw.get<BoxRun>((size_t)nb);
+    std::unique_ptr<BoxRun, decltype(&cudaFreeHost_void)> h_run_owner(nullptr, &cudaFreeHost_void);
+    BoxRun* h_run = nullptr;
+    if (opt.schur_emulation == 1) {
+      CK(cudaMallocHost(&h_run, (size_t)std::max(nb, 1) * sizeof(BoxRun)));
+      h_run_owner.reset(h_run);
+    }
     CK(cudaMemsetAsync(d_run, 0, nb * sizeof(BoxRun), st));
     LD.run = d_run;
     LD.nlist = lw.up(nlist, st);
@@ -683,10 +734,17 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       launch_gather_rows(LD, b0, cnt, st);
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
       if (gram_col[sgi]) {
-        if (gram_tc)
-          launch_tc_gram(LD, b0, cnt, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g, amax,
-                         mmax, H->fp32, st);
-        else
+        if (gram_tc) {
+          // Gram tiles from a (exact); the k range from the row bound m_max
+          std::vector<TcBoxSize> bs(cnt);
+          for (int e = 0; e < cnt; ++e) bs[e] = TcBoxSize{desc[b0 + e].a, 0, 0, 0, desc[b0 + e].mmax};
+          std::vector<TcUnit> units;
+          TcPlan pl;
+          tc_plan(kTcGram, bs, units, pl);
+          gram_units.upload(units, st);
+          launch_tc_planned(kTcGram, LD, b0, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g,
+                            H->fp32, gram_units.d, pl, st);
+        } else
           launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
         CK(cudaGetLastError());
         CK(cudaMemsetAsync(d_pc_scratch, 0, (size_t)pplan[sgi].scratch, st));
@@ -699,20 +757,39 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       } else {
         launch_cpqr(LD, b0, cnt, H->fp32, amax, st);
       }
+      // exact sizes of this colour's boxes (the ID fixed s and r): the tcgen05
+      // launches get exact unit lists instead of bounds
+      TcPlan epl[5];
+      if (use_tc) {
+        CK(cudaMemcpyAsync(h_run + b0, d_run + b0, cnt * sizeof(BoxRun), cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<TcBoxSize> bs(cnt);
+        for (int e = 0; e < cnt; ++e) {
+          const BoxRun& q = h_run[b0 + e];
+          bs[e] = TcBoxSize{desc[b0 + e].a, q.s, q.r, q.n, 0};
+        }
+        std::vector<TcUnit> units;
+        for (int w : {kTcG1, kTcG3, kTcW, kTcSchur, kTcXrr}) tc_plan(w, bs, units, epl[w]);
+        elim_units.upload(units, st);
+      }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
       const int kskip = use_tc ? kTcInnerMin : use_oz ? kOzInnerMin : 0;
       launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
       launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc) {
-        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 0, st);
-        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 1, st);
+        launch_tc_planned(kTcG1, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                          false, elim_units.d, epl[kTcG1], st);
+        launch_tc_planned(kTcG3, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                          false, elim_units.d, epl[kTcG3], st);
       } else if (use_oz) {
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 0, st);
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 1, st);
       }
       launch_gemm_xrr(LD, b0, cnt, amax, st, use_tc ? kTcInnerMin : 0);
       if (use_tc)
-        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 4, st);
+        launch_tc_planned(kTcXrr, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                          false, elim_units.d, epl[kTcXrr], st);
       if (gplan[sgi].dist) {
         CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
         CK(launch_gj_dist(LD, d_parts + gplan[sgi].pbeg, gplan[sgi].np, d_gj_scratch, amax, st));
@@ -721,12 +798,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc)
-        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 2, st);
+        launch_tc_planned(kTcW, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                          false, elim_units.d, epl[kTcW], st);
       else if (use_oz)
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 2, st);
       launch_schur_update(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc)
-        launch_tc_elim(LD, b0, cnt, d_tcb + b0, d_tc_slices, d_tc_expo, amax, nmaxm, 3, st);
+        launch_tc_planned(kTcSchur, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                          false, elim_units.d, epl[kTcSchur], st);
       else if (use_oz)
         launch_oz_schur(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, st);
       CK(cudaGetLastError());

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace fmmlu {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -216,13 +218,24 @@ struct TcBoxHost {       // per box of a colour, planned from bounds
 void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_t& expo_off,
                  TcBoxHost& out);
 size_t tc_smem_bytes(int ns);
-// which: 0 = G1 update, 1 = G3 update, 2 = W = X_CR X_RR^{-1}, 3 = Schur update,
-// 4 = X_RR = A_RR - A_RS T
-void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, int amax, int nmax_max, int which, cudaStream_t st);
-void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, int mmax,
-                    bool fp32, cudaStream_t st);
+// problems of the tcgen05 path
+enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5 };
+struct TcUnit {          // one CTA of a tcgen05-path launch
+  int box;               // box index relative to the colour's first box
+  int side;              // 0 = A operand, 1 = B operand (split launches)
+  int x, y;              // row block and k group (split) or tile (product)
+};
+struct TcBoxSize {       // exact (or bounding) sizes of one box on the host
+  int a, s, r, n, kgram;
+};
+struct TcPlan {          // the five launches of one problem: offsets into the unit list
+  int off[5], cnt[5];    // exponents A, B; digits A, B; product tiles
+};
+void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>& units,
+             TcPlan& plan);
+void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
+                       int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
+                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);

@@ -141,18 +141,48 @@ __host__ __device__ constexpr int plo(int d, int ns) { return d > ns - 1 ? d - (
 __host__ __device__ constexpr int phi(int d, int ns) { return d < ns - 1 ? d : ns - 1; }
 __host__ __device__ constexpr int window(int d, int ns) { return 32 / (phi(d, ns) - plo(d, ns) + 1); }
 
-// balanced base-256 digits of v / 2^e (|v| < 2^(e-1)): NS of them, c_0 first
+// balanced base-256 digits of v / 2^e (|v| < 2^(e-1)): NS of them, c_0 first,
+// c_p in [-128, 128]. |v| 2^(8 NS - e) truncated toward zero is read off the
+// bits of v (integer shifts of the significand, no fp64 arithmetic); its bytes
+// are balanced by carrying into the next byte up; the sign is applied last.
 template <int NS>
 __device__ __forceinline__ void balanced_digits(double v, int e, int* c) {
-  long long F = (long long)ldexp(v, 8 * NS - e);   // |F| < 2^(8 NS - 1), toward zero
+  static_assert(NS == 4 || NS == 7, "digit counts of the complex64 / complex128 splits");
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const bool neg = (u >> 63) != 0;
+  const int E = (int)((u >> 52) & 0x7FF);
+  unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  int ex = -1074;                          // zero or subnormal: mant 2^-1074
+  if (E != 0) { mant |= 1ull << 52; ex = E - 1075; }
+  const int sh = ex + 8 * NS - e;          // |v| 2^(8 NS - e) = mant 2^sh < 2^(8 NS - 1)
+  const unsigned long long U = sh >= 0 ? mant << sh : (sh > -64 ? mant >> (-sh) : 0ull);
+  const uint32_t lo = (uint32_t)U, hi = (uint32_t)(U >> 32);
+  int carry = 0;
 #pragma unroll
   for (int i = NS - 1; i >= 1; --i) {
-    int low = (int)(F & 255);
-    if (low >= 128) low -= 256;
-    c[i] = low;
-    F = (F - low) >> 8;
+    const int byte_index = NS - 1 - i;     // byte of U, least significant first
+    const uint32_t word = byte_index < 4 ? lo : hi;
+    int dg = (int)((word >> (8 * (byte_index & 3))) & 255u) + carry;
+    carry = dg >= 128 ? 1 : 0;
+    c[i] = dg - 256 * carry;
   }
-  c[0] = (int)F;
+  {
+    const int byte_index = NS - 1;
+    const uint32_t word = byte_index < 4 ? lo : hi;
+    c[0] = (int)((word >> (8 * (byte_index & 3))) & 255u) + carry;   // <= 128
+  }
+  if (neg) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) c[i] = -c[i];
+  }
+}
+
+// two small integers (|c| <= 128) as a packed bf16 pair, exactly: the fp32
+// value of c has at most 8 significant bits, so its upper half is its bf16
+__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
+  const float fl = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+  const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+  return __byte_perm(__float_as_uint(fl), __float_as_uint(fh), 0x7632);
 }
 
 }  // namespace tc
@@ -323,13 +353,14 @@ __device__ __forceinline__ int tc_exponent(double mx) {
 
 template <class Prob, bool SideB>
 __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-                                                int* expo) {
-  const int b = b0 + blockIdx.z;
+                                                int* expo, const TcUnit* __restrict__ units) {
+  const TcUnit u = units[blockIdx.x];
+  const int b = b0 + u.box;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
   int m, n, k;
   if (!Prob::dims(L, d, rr, m, n, k)) return;
-  const TcBoxHost t = tb[blockIdx.z];
+  const TcBoxHost t = tb[u.box];
   constexpr bool side_b = SideB;
   constexpr bool kcontig = SideB ? Prob::kBk : Prob::kAk;
   const int len = side_b ? n : m;
@@ -338,7 +369,7 @@ __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxH
   int* ex = expo + (side_b ? t.eb_off : t.ea_off);
   const int lane = threadIdx.x & 31;
   if (kcontig) {                 // a warp per row, lanes along k
-    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int row = u.x * 8 + (threadIdx.x >> 5);
     if (row >= lpad) return;
     double mx = 0.0;
     if (row < len)
@@ -353,8 +384,7 @@ __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxH
     }
     if (lane == 0) ex[row] = tc_exponent(mx);
   } else {                       // a thread per row, consecutive rows contiguous
-    const int row = blockIdx.x * 256 + threadIdx.x;
-    if (blockIdx.x * 256 >= lpad) return;
+    const int row = u.x * 256 + threadIdx.x;
     if (row >= lpad) return;
     double mx = 0.0;
     if (row < len)
@@ -370,28 +400,27 @@ __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxH
   }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) {
-  __nv_bfloat162 h = __halves2bfloat162(__int2bfloat16_rn(lo), __int2bfloat16_rn(hi));
-  return *reinterpret_cast<uint32_t*>(&h);
-}
+__device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) { return tc::bf16_pair(lo, hi); }
 
 // grid: x = 32-row groups, y = k-octet groups of 8 (one per warp), z = boxes
 template <class Prob, int NS, bool SideB>
 __global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-                                                   unsigned char* slices, const int* __restrict__ expo) {
-  const int b = b0 + blockIdx.z;
+                                                   unsigned char* slices, const int* __restrict__ expo,
+                                                   const TcUnit* __restrict__ units) {
+  const TcUnit u = units[blockIdx.x];
+  const int b = b0 + u.box;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
   int m, n, k;
   if (!Prob::dims(L, d, rr, m, n, k)) return;
-  const TcBoxHost t = tb[blockIdx.z];
+  const TcBoxHost t = tb[u.box];
   const int len = SideB ? n : m;
   const int lpad = SideB ? (n + tc::kCols - 1) / tc::kCols * tc::kCols
                          : (m + tc::kRows - 1) / tc::kRows * tc::kRows;
   const int KS = (k + 15) / 16;
-  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int ko = blockIdx.y * 8 + (threadIdx.x >> 5);      // k-octet
-  if (blockIdx.x * 32 >= lpad || ko >= 2 * KS) return;
+  const int row = u.x * 32 + (threadIdx.x & 31);
+  const int ko = u.y * 8 + (threadIdx.x >> 5);      // k-octet
+  if (ko >= 2 * KS) return;
   if (row >= lpad) return;
   const int e = expo[(SideB ? t.eb_off : t.ea_off) + row];
   int cr[8][NS], ci[8][NS];
@@ -453,7 +482,8 @@ __global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcB
 template <class Prob, int NS, int DMAX>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_tc_gemm(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-              const unsigned char* __restrict__ slices, const int* __restrict__ expo, TcExtra x) {
+              const unsigned char* __restrict__ slices, const int* __restrict__ expo, TcExtra x,
+              const TcUnit* __restrict__ units) {
   using namespace tc;
   constexpr int kA = NS * 2 * kAChunk, kB = NS * kBChunk, kStage = kA + kB;
   constexpr int kAcc = DMAX + 1;
@@ -461,18 +491,19 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accf[kAcc], bar_accr[kAcc], bar_done;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
-  const int b = b0 + blockIdx.y;
+  const TcUnit unit = units[blockIdx.x];
+  const int b = b0 + unit.box;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
   int m, n, k;
   if (!Prob::dims(L, d, rr, m, n, k)) return;
   const int tms = (m + kRows - 1) / kRows, tns = (n + kCols - 1) / kCols;
-  if ((int)blockIdx.x >= tms * tns) return;
-  const int tm = blockIdx.x % tms, tn = blockIdx.x / tms;
+  if (unit.x >= tms * tns) return;
+  const int tm = unit.x % tms, tn = unit.x / tms;
   const int i0 = tm * kRows, j0 = tn * kCols;
   if (Prob::kUpper && j0 + kCols - 1 < i0) return;   // entirely below the diagonal
   const int KS = (k + 15) / 16;
-  const TcBoxHost t = tb[blockIdx.y];
+  const TcBoxHost t = tb[unit.box];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -651,26 +682,74 @@ void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_
   expo_off += nb * tc::kCols;
 }
 
+// Sizes of problem `which` for one box: the same rules as the device-side
+// dims() of the problem structs (which the kernels re-check).
+static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) {
+  switch (which) {
+    case kTcG1: m = z.r; n = z.a + z.n; k = z.s; return z.r > 0 && z.s >= kTcInnerMin;
+    case kTcG3: m = z.a + z.n; n = z.r; k = z.s; return z.r > 0 && z.s >= kTcInnerMin;
+    case kTcW: m = z.s + z.n; n = z.r; k = z.r; return z.r >= kTcInnerMin;
+    case kTcSchur: m = z.s + z.n; n = m; k = z.r; return z.r >= kTcInnerMin;
+    case kTcXrr: m = z.r; n = z.r; k = z.s; return z.r > 0 && z.s >= kTcInnerMin;
+    case kTcGram: m = z.a; n = z.a; k = z.kgram; return z.a > 0;
+  }
+  return false;
+}
+static bool tc_kcontig(int which, bool side_b) {
+  return side_b || which == kTcG1 || which == kTcGram;
+}
+
+void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>& units,
+             TcPlan& plan) {
+  for (int l = 0; l < 5; ++l) {
+    plan.off[l] = (int)units.size();
+    for (int e = 0; e < (int)boxes.size(); ++e) {
+      int m, n, k;
+      if (!tc_dims_host(which, boxes[e], m, n, k)) continue;
+      const int lpa = (m + tc::kRows - 1) / tc::kRows * tc::kRows;
+      const int lpb = (n + tc::kCols - 1) / tc::kCols * tc::kCols;
+      const int kg = (2 * ((k + 15) / 16) + 7) / 8;
+      if (l < 2) {                       // exponents of side A / B
+        const int lp = l == 0 ? lpa : lpb;
+        const int per = tc_kcontig(which, l == 1) ? 8 : 256;
+        for (int x = 0; x < (lp + per - 1) / per; ++x) units.push_back(TcUnit{e, l, x, 0});
+      } else if (l < 4) {                // digits of side A / B
+        const int lp = l == 2 ? lpa : lpb;
+        for (int x = 0; x < lp / 32; ++x)
+          for (int y = 0; y < kg; ++y) units.push_back(TcUnit{e, l - 2, x, y});
+      } else {                           // product tiles
+        const int tms = lpa / tc::kRows, tns = lpb / tc::kCols;
+        for (int t = 0; t < tms * tns; ++t) {
+          const int i0 = (t % tms) * tc::kRows, j0 = (t / tms) * tc::kCols;
+          if (which == kTcGram && j0 + tc::kCols - 1 < i0) continue;
+          units.push_back(TcUnit{e, 0, t, 0});
+        }
+      }
+    }
+    plan.cnt[l] = (int)units.size() - plan.off[l];
+  }
+}
+
 template <class Prob, int NS, int DMAX>
-static void launch_tc(const char* name, const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb,
-                      void* slices, int* expo, int mmax, int nmax, int kmax, const TcExtra& x,
-                      cudaStream_t st) {
-  if (nb <= 0) return;
+static void launch_tc(const char* name, const LevelDev& L, int b0, const TcBoxHost* d_tb,
+                      void* slices, int* expo, const TcExtra& x, const TcUnit* d_units,
+                      const TcPlan& pl, cudaStream_t st) {
   unsigned char* sl = reinterpret_cast<unsigned char*>(slices);
-  // exponents: a warp per row where k is contiguous, else a thread per row
-  const int pa = (mmax + tc::kRows - 1) / tc::kRows * tc::kRows;
-  const int pb = (nmax + tc::kCols - 1) / tc::kCols * tc::kCols;
-  dim3 gea((unsigned)(Prob::kAk ? (pa + 7) / 8 : (pa + 255) / 256), 1, nb);
-  dim3 geb((unsigned)(Prob::kBk ? (pb + 7) / 8 : (pb + 255) / 256), 1, nb);
-  FMMLU_LAUNCH("tc_split", st, (k_tc_exp<Prob, false><<<gea, 256, 0, st>>>(L, b0, d_tb, expo)));
-  FMMLU_LAUNCH("tc_split", st, (k_tc_exp<Prob, true><<<geb, 256, 0, st>>>(L, b0, d_tb, expo)));
-  dim3 gda((unsigned)((mmax + tc::kRows - 1) / tc::kRows * (tc::kRows / 32)),
-           (unsigned)((2 * ((kmax + 15) / 16) + 7) / 8), nb);
-  dim3 gdb((unsigned)((nmax + 31) / 32), (unsigned)((2 * ((kmax + 15) / 16) + 7) / 8), nb);
-  FMMLU_LAUNCH("tc_split", st,
-               (k_tc_digits<Prob, NS, false><<<gda, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
-  FMMLU_LAUNCH("tc_split", st,
-               (k_tc_digits<Prob, NS, true><<<gdb, 256, 0, st>>>(L, b0, d_tb, sl, expo)));
+  if (pl.cnt[0] > 0)
+    FMMLU_LAUNCH("tc_split", st,
+                 (k_tc_exp<Prob, false><<<pl.cnt[0], 256, 0, st>>>(L, b0, d_tb, expo, d_units + pl.off[0])));
+  if (pl.cnt[1] > 0)
+    FMMLU_LAUNCH("tc_split", st,
+                 (k_tc_exp<Prob, true><<<pl.cnt[1], 256, 0, st>>>(L, b0, d_tb, expo, d_units + pl.off[1])));
+  if (pl.cnt[2] > 0)
+    FMMLU_LAUNCH("tc_split", st,
+                 (k_tc_digits<Prob, NS, false><<<pl.cnt[2], 256, 0, st>>>(L, b0, d_tb, sl, expo,
+                                                                          d_units + pl.off[2])));
+  if (pl.cnt[3] > 0)
+    FMMLU_LAUNCH("tc_split", st,
+                 (k_tc_digits<Prob, NS, true><<<pl.cnt[3], 256, 0, st>>>(L, b0, d_tb, sl, expo,
+                                                                         d_units + pl.off[3])));
+  if (pl.cnt[4] <= 0) return;
   const size_t smem = tc_smem_bytes(NS);
   static bool attr = false;
   if (!attr) {
@@ -678,38 +757,26 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, int nb, const
                          (int)smem);
     attr = true;
   }
-  const int tiles = ((mmax + tc::kRows - 1) / tc::kRows) * ((nmax + tc::kCols - 1) / tc::kCols);
-  dim3 gm((unsigned)tiles, nb);
   FMMLU_LAUNCH(name, st,
-               (k_tc_gemm<Prob, NS, DMAX><<<gm, tc::kThreads, smem, st>>>(L, b0, d_tb, sl, expo, x)));
+               (k_tc_gemm<Prob, NS, DMAX><<<pl.cnt[4], tc::kThreads, smem, st>>>(
+                   L, b0, d_tb, sl, expo, x, d_units + pl.off[4])));
 }
 
-// which: 0 = G1 update, 1 = G3 update, 2 = W, 3 = Schur update, 4 = X_RR
-void launch_tc_elim(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, int amax, int nmax_max, int which, cudaStream_t st) {
-  const TcExtra x{nullptr, nullptr};
-  const int an = amax + nmax_max;
-  if (which == 0)
-    launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, nb, d_tb, slices, expo, amax, an, amax, x, st);
-  if (which == 1)
-    launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, nb, d_tb, slices, expo, an, amax, amax, x, st);
-  if (which == 2)
-    launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, nb, d_tb, slices, expo, an, amax, amax, x, st);
-  if (which == 3)
-    launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, nb, d_tb, slices, expo, an, an, amax, x, st);
-  if (which == 4)
-    launch_tc<TcXrr, 7, 6>("gemm_xrr_tc", L, b0, nb, d_tb, slices, expo, amax, amax, amax, x, st);
-}
-
-void launch_tc_gram(const LevelDev& L, int b0, int nb, const TcBoxHost* d_tb, void* slices,
-                    int* expo, const GramBoxHost* d_gb, double2* gbuf, int amax, int mmax,
-                    bool fp32, cudaStream_t st) {
+void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
+                       int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
+                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st) {
   const TcExtra x{d_gb, gbuf};
-  if (fp32)
-    launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, mmax, x, st);
-  else
-    launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, nb, d_tb, slices, expo, amax, amax, mmax, x,
-                                     st);
+  switch (which) {
+    case kTcG1: launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcG3: launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcW: launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcSchur: launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcXrr: launch_tc<TcXrr, 7, 6>("gemm_xrr_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcGram:
+      if (fp32) launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
+      else launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
+      break;
+  }
 }
 
 }  // namespace fmmlu
