@@ -477,13 +477,45 @@ __global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcB
 }
 
 // ---------------------------------------------------------------------------
-// the product: one CTA per 128 x 32 complex tile
+// the product: persistent CTAs (one per SM) looping over 128 x 32 complex
+// tiles. Barrier phases, window counts and the two-stage operand pipeline
+// run on across tiles, so the producer prefetches the next tile while the
+// current one drains and the epilogue of one tile overlaps the next tile's
+// first MMAs. Every role walks the same unit sequence and skips the same
+// units.
+
+struct TcTile {
+  bool ok;
+  int rel, b, tm, tn, i0, j0, m, n, KS;
+};
+
+template <class Prob>
+__device__ __forceinline__ TcTile tc_tile(const LevelDev& L, int b0, const TcUnit& u) {
+  TcTile T;
+  T.ok = false;
+  T.rel = u.box;
+  T.b = b0 + u.box;
+  int m, n, k;
+  if (!Prob::dims(L, L.desc[T.b], L.run[T.b], m, n, k)) return T;
+  const int tms = (m + tc::kRows - 1) / tc::kRows, tns = (n + tc::kCols - 1) / tc::kCols;
+  if (u.x >= tms * tns) return T;
+  T.tm = u.x % tms;
+  T.tn = u.x / tms;
+  T.i0 = T.tm * tc::kRows;
+  T.j0 = T.tn * tc::kCols;
+  if (Prob::kUpper && T.j0 + tc::kCols - 1 < T.i0) return T;   // below the diagonal
+  T.m = m;
+  T.n = n;
+  T.KS = (k + 15) / 16;
+  T.ok = true;
+  return T;
+}
 
 template <class Prob, int NS, int DMAX>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     k_tc_gemm(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
               const unsigned char* __restrict__ slices, const int* __restrict__ expo, TcExtra x,
-              const TcUnit* __restrict__ units) {
+              const TcUnit* __restrict__ units, int nunits) {
   using namespace tc;
   constexpr int kA = NS * 2 * kAChunk, kB = NS * kBChunk, kStage = kA + kB;
   constexpr int kAcc = DMAX + 1;
@@ -491,19 +523,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_accf[kAcc], bar_accr[kAcc], bar_done;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
-  const TcUnit unit = units[blockIdx.x];
-  const int b = b0 + unit.box;
-  const BoxDesc& d = L.desc[b];
-  const BoxRun rr = L.run[b];
-  int m, n, k;
-  if (!Prob::dims(L, d, rr, m, n, k)) return;
-  const int tms = (m + kRows - 1) / kRows, tns = (n + kCols - 1) / kCols;
-  if (unit.x >= tms * tns) return;
-  const int tm = unit.x % tms, tn = unit.x / tms;
-  const int i0 = tm * kRows, j0 = tn * kCols;
-  if (Prob::kUpper && j0 + kCols - 1 < i0) return;   // entirely below the diagonal
-  const int KS = (k + 15) / 16;
-  const TcBoxHost t = tb[unit.box];
   unsigned char* sm =
       reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -527,27 +546,30 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   volatile int* abort_flag = &s_abort;
 
   if (warp == 0) {
-    // ---- producer: two-stage bulk-copy pipeline
+    // ---- producer: two-stage bulk-copy pipeline over all steps of all tiles
     if (lane == 0) {
-      const unsigned char* srcA = slices + t.a_off + (int64_t)tm * KS * kA;
-      const unsigned char* srcB = slices + t.b_off + (int64_t)tn * KS * kB;
-      int issued = 0;
-      for (int ks = 0; ks < KS; ++ks) {
-        const int s = ks & 1;
-        if (ks >= 2 && !mbar_wait(&bar_empty[s], ((ks >> 1) - 1) & 1, abort_flag)) break;
-        unsigned char* st = sm + s * kStage;
-        mbar_expect_tx(&bar_full[s], (uint32_t)kStage);
-        bulk_g2s(st, srcA + (int64_t)ks * kA, (uint32_t)kA, &bar_full[s]);
-        bulk_g2s(st + kA, srcB + (int64_t)ks * kB, (uint32_t)kB, &bar_full[s]);
-        issued = ks + 1;
+      int g = 0;
+      bool ok = true;
+      for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
+        const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
+        if (!T.ok) continue;
+        const TcBoxHost t = tb[T.rel];
+        const unsigned char* srcA = slices + t.a_off + (int64_t)T.tm * T.KS * kA;
+        const unsigned char* srcB = slices + t.b_off + (int64_t)T.tn * T.KS * kB;
+        for (int ks = 0; ks < T.KS; ++ks, ++g) {
+          const int s = g & 1;
+          if (g >= 2 && !mbar_wait(&bar_empty[s], ((g >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
+          unsigned char* st = sm + s * kStage;
+          mbar_expect_tx(&bar_full[s], (uint32_t)kStage);
+          bulk_g2s(st, srcA + (int64_t)ks * kA, (uint32_t)kA, &bar_full[s]);
+          bulk_g2s(st + kA, srcB + (int64_t)ks * kB, (uint32_t)kB, &bar_full[s]);
+        }
       }
       if (*abort_flag) {
         // let the copies in flight land before the CTA's shared memory goes away
-        for (int ks = issued > 2 ? issued - 2 : 0; ks < issued; ++ks) {
-          const int s = ks & 1;
+        for (int gg = g > 2 ? g - 2 : 0; gg < g; ++gg)
           for (long long i = 0; i < kWaitLimit; ++i)
-            if (mbar_try(&bar_full[s], (ks >> 1) & 1)) break;
-        }
+            if (mbar_try(&bar_full[gg & 1], (gg >> 1) & 1)) break;
       }
     }
   } else if (warp == 1) {
@@ -557,38 +579,44 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       const uint32_t boffA = Prob::kConj ? 0u : 512u;   // B rows for the A_re product
       const uint32_t boffB = Prob::kConj ? 512u : 0u;   // B rows for the A_im product
       const uint64_t dA = sdesc(0, 2048, 128), dB = sdesc(0, 1536, 128);
-      int nwin[kAcc];
-#pragma unroll
-      for (int a = 0; a < kAcc; ++a) nwin[a] = 0;
+      // per accumulator: bit d of `opened` = a window of d was opened before,
+      // bit d of `wpar` = parity of the number of windows of d opened
+      uint32_t opened = 0, wpar = 0;
+      int g = 0;
       bool ok = true;
-      for (int ks = 0; ks < KS && ok; ++ks) {
-        const int s = ks & 1;
-        if (!mbar_wait(&bar_full[s], (ks >> 1) & 1, abort_flag)) { ok = false; break; }
-        fence_after();
-        const uint32_t aS = smem0 + s * kStage, bS = aS + kA;
+      for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
+        const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
+        if (!T.ok) continue;
+        for (int ks = 0; ks < T.KS && ok; ++ks, ++g) {
+          const int s = g & 1;
+          if (!mbar_wait(&bar_full[s], (g >> 1) & 1, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t aS = smem0 + s * kStage, bS = aS + kA;
 #pragma unroll
-        for (int dd = 0; dd < kAcc; ++dd) {
-          const int W = window(dd, NS);
-          const bool start = ks % W == 0;
-          if (start && ks > 0) {
-            if (!mbar_wait(&bar_accr[dd], (nwin[dd] - 1) & 1, abort_flag)) { ok = false; break; }
-            fence_after();
+          for (int dd = 0; dd < kAcc; ++dd) {
+            const int W = window(dd, NS);
+            const bool start = ks % W == 0;
+            if (start && ((opened >> dd) & 1u)) {
+              // the drain of the previous window: phase (windows opened - 1)
+              if (!mbar_wait(&bar_accr[dd], ((wpar >> dd) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+              fence_after();
+            }
+            if (start) { opened |= 1u << dd; wpar ^= 1u << dd; }
+            const uint32_t dt = tmem + 64 * dd;
+            uint32_t acc = start ? 0u : 1u;
+            for (int p = plo(dd, NS); p <= phi(dd, NS); ++p) {
+              const int q = dd - p;
+              const uint32_t ar = aS + (2 * p) * kAChunk, ai = ar + kAChunk;
+              const uint32_t bq = bS + q * kBChunk;
+              mma(dt, dA + (ar >> 4), dB + ((bq + boffA) >> 4), acc);
+              mma(dt, dA + (ai >> 4), dB + ((bq + boffB) >> 4), 1u);
+              acc = 1u;
+            }
+            if ((ks + 1) % W == 0 || ks == T.KS - 1) commit(&bar_accf[dd]);
           }
-          if (start) ++nwin[dd];
-          const uint32_t dt = tmem + 64 * dd;
-          uint32_t acc = start ? 0u : 1u;
-          for (int p = plo(dd, NS); p <= phi(dd, NS); ++p) {
-            const int q = dd - p;
-            const uint32_t ar = aS + (2 * p) * kAChunk, ai = ar + kAChunk;
-            const uint32_t bq = bS + q * kBChunk;
-            mma(dt, dA + (ar >> 4), dB + ((bq + boffA) >> 4), acc);
-            mma(dt, dA + (ai >> 4), dB + ((bq + boffB) >> 4), 1u);
-            acc = 1u;
-          }
-          if ((ks + 1) % W == 0 || ks == KS - 1) commit(&bar_accf[dd]);
+          if (!ok) break;
+          commit(&bar_empty[s]);
         }
-        if (!ok) break;
-        commit(&bar_empty[s]);
       }
       // all MMAs issued by this thread complete before tensor memory is freed
       commit(&bar_done);
@@ -602,49 +630,55 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const int half = ew >> 2;
     const int row = 32 * quarter + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
-    long long xh[16][2], xl[16][2];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) xh[c][0] = xh[c][1] = xl[c][0] = xl[c][1] = 0;
-    int nwin[kAcc];
-#pragma unroll
-    for (int a = 0; a < kAcc; ++a) nwin[a] = 0;
+    uint32_t dpar = 0;   // bit d: parity of the number of windows of d drained
     bool ok = true;
-    for (int ks = 0; ks < KS && ok; ++ks) {
+    for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
+      const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
+      if (!T.ok) continue;
+      long long xh[16][2], xl[16][2];
 #pragma unroll
-      for (int dd = 0; dd < kAcc; ++dd) {
-        const int W = window(dd, NS);
-        if (!((ks + 1) % W == 0 || ks == KS - 1)) continue;
-        if (!mbar_wait(&bar_accf[dd], nwin[dd] & 1, abort_flag)) { ok = false; break; }
-        ++nwin[dd];
-        fence_after();
-        float vr[16], vi[16];
-        tmem_ld16(tl + 64 * dd + 16 * half, vr);
-        tmem_ld16(tl + 64 * dd + 32 + 16 * half, vi);
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_accr[dd]);
-        const bool hi = dd <= 2;
-        const int sh = hi ? 8 * (2 - dd) : 8 * (DMAX - dd);
+      for (int c = 0; c < 16; ++c) xh[c][0] = xh[c][1] = xl[c][0] = xl[c][1] = 0;
+      for (int ks = 0; ks < T.KS && ok; ++ks) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long r0 = (long long)__float2int_rn(vr[c]) << sh;
-          const long long r1 = (long long)__float2int_rn(vi[c]) << sh;
-          if (hi) { xh[c][0] += r0; xh[c][1] += r1; }
-          else { xl[c][0] += r0; xl[c][1] += r1; }
+        for (int dd = 0; dd < kAcc; ++dd) {
+          const int W = window(dd, NS);
+          if (!((ks + 1) % W == 0 || ks == T.KS - 1)) continue;
+          if (!mbar_wait(&bar_accf[dd], (dpar >> dd) & 1u, abort_flag)) { ok = false; break; }
+          dpar ^= 1u << dd;
+          fence_after();
+          float vr[16], vi[16];
+          tmem_ld16(tl + 64 * dd + 16 * half, vr);
+          tmem_ld16(tl + 64 * dd + 32 + 16 * half, vi);
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_accr[dd]);
+          const bool hi = dd <= 2;
+          const int sh = hi ? 8 * (2 - dd) : 8 * (DMAX - dd);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const long long r0 = (long long)__float2int_rn(vr[c]) << sh;
+            const long long r1 = (long long)__float2int_rn(vi[c]) << sh;
+            if (hi) { xh[c][0] += r0; xh[c][1] += r1; }
+            else { xl[c][0] += r0; xl[c][1] += r1; }
+          }
         }
       }
-    }
-    if (ok && !*abort_flag) {
-      const int i = i0 + row;
-      if (i < m) {
+      if (!ok || *abort_flag) break;
+      const int i = T.i0 + row;
+      if (i < T.m) {
+        const TcBoxHost t = tb[T.rel];
+        const BoxDesc& d = L.desc[T.b];
+        const BoxRun rr = L.run[T.b];
         const int ei = expo[t.ea_off + i];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int j = j0 + 16 * half + c;
-          if (j >= n) continue;
+          const int j = T.j0 + 16 * half + c;
+          if (j >= T.n) continue;
           const int E = ei + expo[t.eb_off + j];
-          const double vr = ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
-          const double vi = ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
+          const double vr =
+              ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
+          const double vi =
+              ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
           Prob::epi(L, d, rr, x, i, j, vr, vi);
         }
       }
@@ -757,9 +791,16 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, const TcBoxHo
                          (int)smem);
     attr = true;
   }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int grid = std::min(pl.cnt[4], std::max(sms, 1));   // one persistent CTA per SM
   FMMLU_LAUNCH(name, st,
-               (k_tc_gemm<Prob, NS, DMAX><<<pl.cnt[4], tc::kThreads, smem, st>>>(
-                   L, b0, d_tb, sl, expo, x, d_units + pl.off[4])));
+               (k_tc_gemm<Prob, NS, DMAX><<<grid, tc::kThreads, smem, st>>>(
+                   L, b0, d_tb, sl, expo, x, d_units + pl.off[4], pl.cnt[4])));
 }
 
 void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
