@@ -142,6 +142,8 @@ struct UnitBuf {
   }
 };
 
+constexpr int kRowChunkHost = 16;   // rows per CTA of the solve's R and S products
+
 inline uint64_t pkey(int x, int y) { return ((uint64_t)(uint32_t)x << 32) | (uint32_t)y; }
 
 void default_opts(fmmlu_opts* o) {
@@ -893,14 +895,16 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         if (rr.r == 0) continue;
         int64_t ld3 = d.a + d.nmax;
         SolveBox sb;
-        sb.r = rr.r; sb.s = rr.s; sb.n = rr.n; sb.pad_ = 0;
+        sb.r = rr.r; sb.s = rr.s; sb.n = rr.n; sb.zoff = (int)part;
         sb.idx = d_iarena + d.idx_off;
         sb.T = d_arena + d.T_off; sb.ldT = d.a;
         sb.Xinv = d_arena + d.Xinv_off; sb.ldX = d.a;
         sb.XCR = d_arena + d.G3_off + (int64_t)rr.s * ld3; sb.ldL = (int)ld3;
         sb.XRC = d_arena + d.G1_off + rr.s; sb.ldU = d.a;
         sb.item_beg = (int)items.size();
-        for (int c0 = 0; c0 < rr.s + rr.n; c0 += kSweepChunk) {
+        // at least one C chunk per box: its partial slots double as the
+        // box's z scratch, and it stores b_R = z in the forward sweep
+        for (int c0 = 0; c0 == 0 || c0 < rr.s + rr.n; c0 += kSweepChunk) {
           items.push_back(SweepItem{(int)plan.size(), c0, std::min(rr.s + rr.n, c0 + kSweepChunk),
                                     (int)part});
           part += rr.r;
@@ -922,6 +926,17 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         SweepSeg sg;
         sg.b0 = b0p; sg.nb = cnt;
         sg.i0 = i0p; sg.ni = (int)items.size() - i0p;
+        // row chunks of the R and S products
+        sg.ri0 = (int)items.size();
+        for (int q = b0p; q < b0p + cnt; ++q)
+          for (int k0 = 0; k0 < plan[q].r; k0 += kRowChunkHost)
+            items.push_back(SweepItem{q, k0, std::min(plan[q].r, k0 + kRowChunkHost), 0});
+        sg.nri = (int)items.size() - sg.ri0;
+        sg.si0 = (int)items.size();
+        for (int q = b0p; q < b0p + cnt; ++q)
+          for (int i0s = 0; i0s < plan[q].s; i0s += kRowChunkHost)
+            items.push_back(SweepItem{q, i0s, std::min(plan[q].s, i0s + kRowChunkHost), 0});
+        sg.nsi = (int)items.size() - sg.si0;
         sg.rmax = rmax; sg.smax = smax; sg.part = part;
         sg.flops_c = fc; sg.bytes_c = bc; sg.flops_b = fb; sg.bytes_b = bb;
         sg.bytes_per_rhs = seg_vbytes;

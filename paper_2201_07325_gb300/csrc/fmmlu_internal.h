@@ -91,7 +91,7 @@ struct LevelDev {   // device state of a level
 
 // one per eliminated box, in elimination order (solve plan)
 struct SolveBox {
-  int r, s, n, pad_;
+  int r, s, n, zoff;       // zoff: the box's r scratch values (its first chunk's partials)
   int item_beg, item_cnt;  // chunks of C = [S | N] (SweepItem list)
   const int* idx;          // [R | S | N]
   const double2* T;  int ldT;
@@ -110,7 +110,9 @@ struct SweepItem {
 // one colour of one level in the solve plan
 struct SweepSeg {
   int b0, nb;    // boxes [b0, b0 + nb) of the SolveBox array
-  int i0, ni;    // items [i0, i0 + ni)
+  int i0, ni;    // C-chunk items [i0, i0 + ni)
+  int ri0, nri;  // R-row chunk items
+  int si0, nsi;  // S-row chunk items
   int rmax, smax;
   int64_t part;  // partial sums needed per right-hand side
   double flops_c, bytes_c;   // per sweep: X_CR / X_RC products (per rhs: flops)

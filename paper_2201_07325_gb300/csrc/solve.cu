@@ -38,55 +38,173 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs, 
   FMMLU_LAUNCH("scatter_vec", st, k_scatter_vec<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(v, perm, n, x));
 }
 
-// Box sweeps, two launches per colour and direction:
-//   forward:  k_fwd_z (one CTA per box)   z = op(X_RR^{-1}) (b_R - op(T)^T b_S), b_R = z
-//             k_fwd_c (one CTA per chunk) b_C -= op(X_CR) z over a chunk of C rows
-//   backward: k_bwd_t (one CTA per chunk) partial = op(X_RC) x_C over a chunk of C
-//             k_bwd_x (one CTA per box)   x_R -= op(X_RR^{-1}) sum(partials); x_S -= op(T) x_R
+// Box sweeps, three launches per colour and direction, every product split
+// into row chunks so that one large box uses many SMs (GB300's fp64 rate per
+// SM is ~4 GFLOP/s, so one CTA per box would be bound by a single SM):
+//   forward:  k_sw_y  (R chunks)  b_R -= op(T)^T b_S
+//             k_sw_z  (R chunks)  z = op(X_RR^{-1}) b_R  (into the box's scratch)
+//             k_fwd_c (C chunks)  b_C -= op(X_CR) z; the first chunk stores b_R = z
+//   backward: k_bwd_t (C chunks)  partial = op(X_RC) x_C
+//             k_sw_xr (R chunks)  x_R -= op(X_RR^{-1}) sum(partials)
+//             k_sw_xs (S chunks)  x_S -= op(T) x_R
 // op() is the identity for A^{-1}; for A^{-H} the roles are (X_RC^H, X_CR^H,
-// X_RR^{-H}, conj(T)). Chunks let one large box use many SMs.
+// X_RR^{-H}, conj(T)).
 
-__global__ void __launch_bounds__(256) k_fwd_z(const SolveBox* __restrict__ boxes, int b0,
-                                               double2* __restrict__ v, int64_t n, int adjoint) {
-  extern __shared__ double2 sh[];
-  const SolveBox B = boxes[b0 + blockIdx.x];
-  const int r = B.r, s = B.s;
-  double2* vc = v + blockIdx.y * n;
-  double2* bR = sh;                 // r
-  double2* bS = sh + B.r;           // s
-  const int* Ridx = B.idx;
-  const int* Sidx = B.idx + r;
-  for (int i = threadIdx.x; i < s; i += blockDim.x) bS[i] = vc[Sidx[i]];
-  __syncthreads();
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double2 acc = vc[Ridx[k]];
-    const double2* Tk = B.T + (int64_t)k * B.ldT;
-    for (int i = 0; i < s; ++i) {
-      double2 tv = adjoint ? cconj(Tk[i]) : Tk[i];
-      cfms(acc, tv, bS[i]);
+constexpr int kRowChunk = 16;   // output rows per CTA of the R and S products
+
+// out[k - k0] = sum_l op(M)(k, l) x[l] for k in [k0, k0 + kc), kc <= 16, with
+// 256 threads and x in shared memory. kRows: element (k, l) at M[k + l ld]
+// (a half-warp reads 16 consecutive k); else at M[l + k ld] (16 consecutive
+// l). cj conjugates the matrix element.
+template <bool kRows>
+__device__ __forceinline__ void chunk_mv(const double2* __restrict__ M, int64_t ld, bool cj,
+                                         const double2* x, int L, int k0, int kc, double2* red,
+                                         double2* out) {
+  const int t = threadIdx.x;
+  double2 acc = mk(0.0, 0.0);
+  if (kRows) {
+    const int row = t & 15, g = t >> 4;
+    if (row < kc) {
+      const double2* Mr = M + (k0 + row);
+      for (int l = g; l < L; l += 16) {
+        const double2 m = Mr[(int64_t)l * ld];
+        if (cj) cfma_cj(acc, m, x[l]); else cfma(acc, m, x[l]);
+      }
     }
-    bR[k] = acc;
+    red[t] = acc;
+    __syncthreads();
+    if (t < kRowChunk) {
+      double2 sum = mk(0.0, 0.0);
+      for (int q = 0; q < 16; ++q) sum = cadd(sum, red[q * 16 + t]);
+      out[t] = sum;
+    }
+  } else {
+    const int row = t >> 4, ln = t & 15;
+    if (row < kc) {
+      const double2* Mc = M + (int64_t)(k0 + row) * ld;
+      for (int l = ln; l < L; l += 16) {
+        const double2 m = Mc[l];
+        if (cj) cfma_cj(acc, m, x[l]); else cfma(acc, m, x[l]);
+      }
+    }
+    for (int o = 8; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (ln == 0) out[row] = acc;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+}
+
+// forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
+__global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes,
+                                              const SweepItem* __restrict__ items, int i0,
+                                              double2* __restrict__ v, int64_t n, int adjoint) {
+  extern __shared__ double2 sh[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  double2* vc = v + blockIdx.y * n;
+  double2* red = sh;            // 256
+  double2* out = sh + 256;      // 16
+  double2* bS = sh + 272;       // s
+  const int* Ridx = B.idx;
+  const int* Sidx = B.idx + B.r;
+  for (int i = threadIdx.x; i < B.s; i += blockDim.x) bS[i] = vc[Sidx[i]];
+  __syncthreads();
+  const int kc = it.c1 - it.c0;
+  chunk_mv<false>(B.T, B.ldT, adjoint != 0, bS, B.s, it.c0, kc, red, out);
+  if (threadIdx.x < kc) {
+    const int dof = Ridx[it.c0 + threadIdx.x];
+    vc[dof] = csub(vc[dof], out[threadIdx.x]);
+  }
+}
+
+// forward: z = op(X_RR^{-1}) b_R for the chunk's rows, into the box's scratch
+__global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes,
+                                              const SweepItem* __restrict__ items, int i0,
+                                              const double2* __restrict__ v, int64_t n,
+                                              double2* __restrict__ zbuf, int64_t zstride,
+                                              int adjoint) {
+  extern __shared__ double2 sh[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  const double2* vc = v + blockIdx.y * n;
+  double2* red = sh;
+  double2* out = sh + 256;
+  double2* y = sh + 272;        // r
+  for (int k = threadIdx.x; k < B.r; k += blockDim.x) y[k] = vc[B.idx[k]];
+  __syncthreads();
+  const int kc = it.c1 - it.c0;
+  if (!adjoint) chunk_mv<true>(B.Xinv, B.ldX, false, y, B.r, it.c0, kc, red, out);
+  else chunk_mv<false>(B.Xinv, B.ldX, true, y, B.r, it.c0, kc, red, out);
+  if (threadIdx.x < kc) zbuf[blockIdx.y * zstride + B.zoff + it.c0 + threadIdx.x] = out[threadIdx.x];
+}
+
+// backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = sum of the partials
+__global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxes,
+                                               const SweepItem* __restrict__ items, int i0,
+                                               double2* __restrict__ v, int64_t n,
+                                               const double2* __restrict__ partial,
+                                               int64_t pstride, int adjoint) {
+  extern __shared__ double2 sh[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  double2* vc = v + blockIdx.y * n;
+  const double2* pc = partial + blockIdx.y * pstride;
+  double2* red = sh;
+  double2* out = sh + 256;
+  double2* tt = sh + 272;       // r
+  for (int k = threadIdx.x; k < B.r; k += blockDim.x) {
     double2 acc = mk(0.0, 0.0);
-    if (!adjoint)
-      for (int l = 0; l < r; ++l) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], bR[l]);
-    else
-      for (int l = 0; l < r; ++l) cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], bR[l]);
-    vc[Ridx[k]] = acc;
+    for (int q = B.item_beg; q < B.item_beg + B.item_cnt; ++q) acc = cadd(acc, pc[items[q].part + k]);
+    tt[k] = acc;
+  }
+  __syncthreads();
+  const int kc = it.c1 - it.c0;
+  if (!adjoint) chunk_mv<true>(B.Xinv, B.ldX, false, tt, B.r, it.c0, kc, red, out);
+  else chunk_mv<false>(B.Xinv, B.ldX, true, tt, B.r, it.c0, kc, red, out);
+  if (threadIdx.x < kc) {
+    const int dof = B.idx[it.c0 + threadIdx.x];
+    vc[dof] = csub(vc[dof], out[threadIdx.x]);
+  }
+}
+
+// backward: x_S[i] -= sum_k op(T)(i, k) x_R[k] for the chunk's rows i
+__global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxes,
+                                               const SweepItem* __restrict__ items, int i0,
+                                               double2* __restrict__ v, int64_t n, int adjoint) {
+  extern __shared__ double2 sh[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  double2* vc = v + blockIdx.y * n;
+  double2* red = sh;
+  double2* out = sh + 256;
+  double2* xr = sh + 272;       // r
+  for (int k = threadIdx.x; k < B.r; k += blockDim.x) xr[k] = vc[B.idx[k]];
+  __syncthreads();
+  const int kc = it.c1 - it.c0;
+  chunk_mv<true>(B.T, B.ldT, adjoint != 0, xr, B.r, it.c0, kc, red, out);
+  if (threadIdx.x < kc) {
+    const int dof = B.idx[B.r + it.c0 + threadIdx.x];
+    vc[dof] = csub(vc[dof], out[threadIdx.x]);
   }
 }
 
 __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
-                                               double2* __restrict__ v, int64_t n, int adjoint) {
+                                               double2* __restrict__ v, int64_t n,
+                                               const double2* __restrict__ zbuf, int64_t zstride,
+                                               int adjoint) {
   extern __shared__ double2 z[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int r = B.r;
   double2* vc = v + blockIdx.y * n;
-  for (int k = threadIdx.x; k < r; k += blockDim.x) z[k] = vc[B.idx[k]];
+  const double2* zc = zbuf + blockIdx.y * zstride + B.zoff;
+  for (int k = threadIdx.x; k < r; k += blockDim.x) {
+    z[k] = zc[k];
+    if (it.c0 == 0) vc[B.idx[k]] = z[k];   // b_R = z, once per box
+  }
   __syncthreads();
   const int* Cidx = B.idx + r;
   for (int i = it.c0 + threadIdx.x; i < it.c1; i += blockDim.x) {
@@ -140,54 +258,12 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   }
 }
 
-__global__ void __launch_bounds__(256) k_bwd_x(const SolveBox* __restrict__ boxes, int b0,
-                                               const SweepItem* __restrict__ items,
-                                               double2* __restrict__ v, int64_t n,
-                                               const double2* __restrict__ partial,
-                                               int64_t pstride, int adjoint) {
-  extern __shared__ double2 sh[];
-  const SolveBox B = boxes[b0 + blockIdx.x];
-  const int r = B.r, s = B.s;
-  double2* vc = v + blockIdx.y * n;
-  const double2* pc = partial + blockIdx.y * pstride;
-  double2* t = sh;        // r
-  double2* xr = sh + r;   // r
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int q = B.item_beg; q < B.item_beg + B.item_cnt; ++q) acc = cadd(acc, pc[items[q].part + k]);
-    t[k] = acc;
-  }
-  __syncthreads();
-  const int* Ridx = B.idx;
-  const int* Sidx = B.idx + r;
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    if (!adjoint)
-      for (int l = 0; l < r; ++l) cfma(acc, B.Xinv[k + (int64_t)l * B.ldX], t[l]);
-    else
-      for (int l = 0; l < r; ++l) cfma_cj(acc, B.Xinv[l + (int64_t)k * B.ldX], t[l]);
-    double2 x = csub(vc[Ridx[k]], acc);
-    xr[k] = x;
-    vc[Ridx[k]] = x;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int k = 0; k < r; ++k) {
-      double2 tv = B.T[i + (int64_t)k * B.ldT];
-      cfma(acc, adjoint ? cconj(tv) : tv, xr[k]);
-    }
-    vc[Sidx[i]] = csub(vc[Sidx[i]], acc);
-  }
-}
-
 static void set_smem_attr() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(k_fwd_z, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_fwd_c, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_bwd_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_bwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  for (const void* f : {(const void*)k_sw_y, (const void*)k_sw_z, (const void*)k_sw_xr,
+                        (const void*)k_sw_xs, (const void*)k_fwd_c, (const void*)k_bwd_t})
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   done = true;
 }
 
@@ -196,21 +272,30 @@ void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg&
                   double2* partial, int64_t pstride, cudaStream_t st) {
   if (sg.nb <= 0) return;
   set_smem_attr();
-  int adj = adjoint ? 1 : 0;
+  const int adj = adjoint ? 1 : 0;
+  const size_t base = (size_t)(256 + kRowChunk) * sizeof(double2);
   if (!backward) {
-    size_t sm1 = (size_t)(sg.rmax + sg.smax) * sizeof(double2);
-    FMMLU_LAUNCH("sweep_fwd", st, k_fwd_z<<<dim3(sg.nb, nrhs), 256, sm1, st>>>(boxes, sg.b0, v, n, adj));
-    size_t sm2 = (size_t)sg.rmax * sizeof(double2);
-    if (sg.ni > 0)
-      FMMLU_LAUNCH("sweep_fwd_c", st, k_fwd_c<<<dim3(sg.ni, nrhs), 256, sm2, st>>>(boxes, items, sg.i0, v, n, adj));
+    if (sg.smax > 0)
+      FMMLU_LAUNCH("sweep_fwd", st,
+                   k_sw_y<<<dim3(sg.nri, nrhs), 256, base + sg.smax * sizeof(double2), st>>>(
+                       boxes, items, sg.ri0, v, n, adj));
+    FMMLU_LAUNCH("sweep_fwd", st,
+                 k_sw_z<<<dim3(sg.nri, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
+                     boxes, items, sg.ri0, v, n, partial, pstride, adj));
+    FMMLU_LAUNCH("sweep_fwd_c", st,
+                 k_fwd_c<<<dim3(sg.ni, nrhs), 256, (size_t)sg.rmax * sizeof(double2), st>>>(
+                     boxes, items, sg.i0, v, n, partial, pstride, adj));
   } else {
     size_t sm1 = (size_t)(kSweepChunk + 256) * sizeof(double2);
-    if (sg.ni > 0)
-      FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
-                                                                                 partial, pstride, adj));
-    size_t sm2 = (size_t)(2 * sg.rmax) * sizeof(double2);
-    FMMLU_LAUNCH("sweep_bwd", st, k_bwd_x<<<dim3(sg.nb, nrhs), 256, sm2, st>>>(boxes, sg.b0, items, v, n,
-                                                                             partial, pstride, adj));
+    FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
+                                                                               partial, pstride, adj));
+    FMMLU_LAUNCH("sweep_bwd", st,
+                 k_sw_xr<<<dim3(sg.nri, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
+                     boxes, items, sg.ri0, v, n, partial, pstride, adj));
+    if (sg.nsi > 0)
+      FMMLU_LAUNCH("sweep_bwd", st,
+                   k_sw_xs<<<dim3(sg.nsi, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
+                       boxes, items, sg.si0, v, n, adj));
   }
 }
 
