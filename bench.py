@@ -311,7 +311,7 @@ def run_gpu(args, rank, world):
     dname, d = dom
     fp32_path = precision == pkg.PRECISION_MIXED or (precision == pkg.PRECISION_AUTO
                                                      and eps >= 1e-5)
-    fp32_kernels = {"cpqr", "assemble_id"} if fp32_path else set()
+    fp32_kernels = ({"cpqr", "assemble_id"} if fp32_path else set()) | {"xrr_inverse32"}
     peaks = measured_peaks()
     if is_tensor_kernel(dname):
         # exact-split products on the bf16 tensor cores: the bf16 flops of the

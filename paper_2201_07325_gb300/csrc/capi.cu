@@ -523,6 +523,30 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     LD.proxy_factor = opt.proxy_radius_factor;
     LD.eps = eps_id;
     LD.status = d_status;
+    // refinement of X_RR^{-1} (tcgen05 path): per colour an X_RR copy and a
+    // product scratch of a^2 each per box
+    int ns_rmax = 0;
+    if (opt.schur_emulation == 1) {   // the tcgen05 path
+      for (int r = kNsMin; r <= 4096; r += 8)
+        if (gj32_cluster_size(r) > 0) ns_rmax = r; else break;
+    }
+    {
+      std::vector<int64_t> nso(nb, 0);
+      int64_t ns_max = 0;
+      if (ns_rmax >= kNsMin)
+        for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+          int64_t o = 0;
+          for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
+            nso[e] = o;
+            o += 2 * (int64_t)desc[e].a * desc[e].a;
+          }
+          ns_max = std::max(ns_max, o);
+        }
+      LD.nsbuf = ns_rmax >= kNsMin ? lw.get<double2>((size_t)ns_max) : nullptr;
+      LD.ns_off = lw.up(nso, st);
+      LD.ns_err = lw.get<unsigned long long>((size_t)nb);
+      LD.ns_rmax = ns_rmax;
+    }
     // CPQR plan per colour: boxes share the co-resident CTAs in proportion to
     // their work (rows x a^2); colours with many boxes use one CTA per box.
     struct ColPlan { int pbeg = 0, np = 0; int64_t scratch = 0; bool dist = false; };
@@ -761,7 +785,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       // exact sizes of this colour's boxes (the ID fixed s and r): the tcgen05
       // launches get exact unit lists instead of bounds
-      TcPlan epl[5];
+      TcPlan epl[8];
+      int ns_off0 = 0, ns_cnt = 0, ns_rmax_c = 0;   // boxes whose X_RR^{-1} is refined
       if (use_tc) {
         CK(cudaMemcpyAsync(h_run + b0, d_run + b0, cnt * sizeof(BoxRun), cudaMemcpyDeviceToHost,
                            st));
@@ -769,10 +794,22 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         std::vector<TcBoxSize> bs(cnt);
         for (int e = 0; e < cnt; ++e) {
           const BoxRun& q = h_run[b0 + e];
-          bs[e] = TcBoxSize{desc[b0 + e].a, q.s, q.r, q.n, 0};
+          bs[e] = TcBoxSize{desc[b0 + e].a, q.s, q.r, q.n, 0, ns_rmax};
         }
         std::vector<TcUnit> units;
         for (int w : {kTcG1, kTcG3, kTcW, kTcSchur, kTcXrr}) tc_plan(w, bs, units, epl[w]);
+        if (ns_rmax >= kNsMin) {
+          for (int w : {kTcNsY, kTcNsX}) tc_plan(w, bs, units, epl[w]);
+          ns_off0 = (int)units.size();
+          for (int e = 0; e < cnt; ++e) {
+            const int r = h_run[b0 + e].r;
+            if (r >= kNsMin && r <= ns_rmax) {
+              units.push_back(TcUnit{e, 0, 0, 0});
+              ns_rmax_c = std::max(ns_rmax_c, r);
+            }
+          }
+          ns_cnt = (int)units.size() - ns_off0;
+        }
         elim_units.upload(units, st);
       }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
@@ -792,11 +829,43 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (use_tc)
         launch_tc_planned(kTcXrr, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
                           false, elim_units.d, epl[kTcXrr], st);
-      if (gplan[sgi].dist) {
-        CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
-        CK(launch_gj_dist(LD, d_parts + gplan[sgi].pbeg, gplan[sgi].np, d_gj_scratch, amax, st));
-      } else {
-        launch_xrr_inverse(LD, b0, cnt, amax, st);
+      // X_RR^{-1}: boxes with kNsMin <= r <= ns_rmax by an fp32 inverse over a
+      // thread-block cluster and two Newton-Schulz steps on the tensor cores
+      // (boxes whose residual stays above 1e-9 are inverted again in fp64);
+      // the other boxes by fp64 Gauss-Jordan
+      bool ns_done = false;
+      if (ns_cnt > 0) {
+        const int P = gj32_cluster_size(ns_rmax_c);
+        cudaError_t eg = P > 0 ? launch_gj32(LD, b0, elim_units.d + ns_off0, ns_cnt, ns_rmax_c, P, st)
+                               : cudaErrorNotSupported;
+        if (eg == cudaSuccess) {
+          launch_xrr_inverse(LD, b0, cnt, amax, st, kNsMin, ns_rmax);
+          auto ns = [&](int w) {
+            launch_tc_planned(w, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr, false,
+                              elim_units.d, epl[w], st);
+          };
+          // three steps; the last product's residual e bounds the result's
+          // by (r e)^2, so e <= 1e-9 leaves it below ~1e-12 for r <= 640
+          ns(kTcNsY);
+          ns(kTcNsX);
+          ns(kTcNsY);
+          ns(kTcNsX);
+          CK(cudaMemsetAsync(LD.ns_err + b0, 0, (size_t)cnt * sizeof(unsigned long long), st));
+          ns(kTcNsY);
+          ns(kTcNsX);
+          launch_ns_fallback(LD, b0, elim_units.d + ns_off0, ns_cnt, amax, 1e-9, st);
+          ns_done = true;
+        } else if (eg != cudaErrorNotSupported) {
+          CK(eg);
+        }
+      }
+      if (!ns_done) {
+        if (gplan[sgi].dist) {
+          CK(cudaMemsetAsync(d_gj_scratch, 0, (size_t)gplan[sgi].scratch, st));
+          CK(launch_gj_dist(LD, d_parts + gplan[sgi].pbeg, gplan[sgi].np, d_gj_scratch, amax, st));
+        } else {
+          launch_xrr_inverse(LD, b0, cnt, amax, st);
+        }
       }
       launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc)
@@ -869,7 +938,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                          (use_tc && tc_s ? c_tc : 8.0) * r_ * r_ * s_,
                          16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
         if (use_tc && tc_s) H->prof.add_work(split_name, 0, split(r_, r_, s_));
-        H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
+        if (use_tc && ns_rmax >= kNsMin && rr.r >= kNsMin && rr.r <= ns_rmax) {
+          // fp32 Gauss-Jordan, then two Newton-Schulz steps (two products each)
+          H->prof.add_work("xrr_inverse32", 8.0 * r_ * r_ * r_, 16.0 * 3 * r_ * r_);
+          H->prof.add_work("ns_tc", 6.0 * c_tc * r_ * r_ * r_, 16.0 * 6 * 3 * r_ * r_);
+          H->prof.add_work(split_name, 0, 6.0 * split(r_, r_, r_));
+        } else {
+          H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
+        }
         H->prof.add_work(tc_r ? "gemm_w_tc" : "gemm_w", (tc_r ? c_tc : 8.0) * (s_ + n_) * r_ * r_,
                          16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
         H->prof.add_work(tc_r ? "schur_tc" : "schur_update",
@@ -945,10 +1021,25 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
     }
     double lms = lt.ms();
+    // refinement of X_RR^{-1}: boxes refined, largest final-step residual, fallbacks
+    int ns_boxes = 0, ns_fallback = 0;
+    double ns_worst = 0.0;
+    if (ns_rmax >= kNsMin) {
+      std::vector<unsigned long long> errs = ddownload(LD.ns_err, (size_t)nb, st);
+      for (int e = 0; e < nb; ++e) {
+        if (run[e].r < kNsMin || run[e].r > ns_rmax) continue;
+        double v;
+        std::memcpy(&v, &errs[e], sizeof(v));
+        ++ns_boxes;
+        ns_worst = std::max(ns_worst, v);
+        if (!(v <= 1e-9)) ++ns_fallback;
+      }
+    }
     if (opt.verbose)
-      std::fprintf(stderr, "[fmmlu] level %d: boxes %d colours %d current %zu sum_a %lld sum_s %lld max_a %lld max_r %lld pool %.1f MB %.1f ms\n",
+      std::fprintf(stderr, "[fmmlu] level %d: boxes %d colours %d current %zu sum_a %lld sum_s %lld max_a %lld max_r %lld pool %.1f MB %.1f ms; refined inverses %d (worst residual %.1e, fp64 again %d)\n",
                    lev, nb, HL.ncolours, L->cur.size(), (long long)sum_a, (long long)sum_s,
-                   (long long)max_a, (long long)max_r, L->pool_size * 16.0 / 1e6, lms);
+                   (long long)max_a, (long long)max_r, L->pool_size * 16.0 / 1e6, lms, ns_boxes,
+                   ns_worst, ns_fallback);
     js << (first_level ? "" : ", ") << "{\"level\": " << lev << ", \"boxes\": " << nb
        << ", \"colours\": " << HL.ncolours << ", \"current\": " << L->cur.size()
        << ", \"sum_a\": " << sum_a << ", \"sum_s\": " << sum_s << ", \"max_a\": " << max_a

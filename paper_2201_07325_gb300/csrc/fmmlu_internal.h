@@ -87,7 +87,15 @@ struct LevelDev {   // device state of a level
   double proxy_factor;
   double eps;
   int* status;
+  // X_RR^{-1} by fp32 inversion + Newton-Schulz refinement (boxes with
+  // kNsMin <= r <= ns_rmax): per box (descriptor index) the offset of its
+  // X_RR copy and product scratch (2 a^2 values) and its refinement residual
+  double2* nsbuf;
+  const int64_t* ns_off;
+  unsigned long long* ns_err;   // max |I - X_RR X_1| per box, as double bits
+  int ns_rmax;
 };
+constexpr int kNsMin = 32;      // smallest r refined on the tensor cores
 
 // one per eliminated box, in elimination order (solve plan)
 struct SolveBox {
@@ -221,7 +229,8 @@ void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_
                  TcBoxHost& out);
 size_t tc_smem_bytes(int ns);
 // problems of the tcgen05 path
-enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5 };
+enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5, kTcNsY = 6,
+       kTcNsX = 7 };
 struct TcUnit {          // one CTA of a tcgen05-path launch
   int box;               // box index relative to the colour's first box
   int side;              // 0 = A operand, 1 = B operand (split launches)
@@ -229,6 +238,7 @@ struct TcUnit {          // one CTA of a tcgen05-path launch
 };
 struct TcBoxSize {       // exact (or bounding) sizes of one box on the host
   int a, s, r, n, kgram;
+  int nsmax;             // largest r refined by Newton-Schulz
 };
 struct TcPlan {          // the five launches of one problem: offsets into the unit list
   int off[5], cnt[5];    // exponents A, B; digits A, B; product tiles
@@ -238,6 +248,17 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
 void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
                        int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
                        const TcUnit* d_units, const TcPlan& pl, cudaStream_t st);
+// gj_dist.cu: fp32 Gauss-Jordan of X_RR over a thread-block cluster per box
+// (units: one per box, TcUnit::box relative to b0); writes the fp32 inverse to
+// Xinv (as complex128) and a complex128 copy of X_RR to nsbuf
+size_t gj32_smem(int rmax, int P);
+int gj32_cluster_size(int rmax);                 // 0: no cluster shape fits
+cudaError_t launch_gj32(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, int rmax,
+                        int P, cudaStream_t st);
+// linalg.cu: boxes of the refinement whose residual exceeds `thr` are
+// inverted again in fp64 from the stored copy of X_RR (one CTA per box)
+void launch_ns_fallback(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, int amax,
+                        double thr, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);
@@ -249,7 +270,8 @@ void launch_gemm_g1(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
 void launch_gemm_g3(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                     cudaStream_t st, int kskip = 0);
 void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st, int kskip = 0);
-void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st);
+void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st,
+                        int skip_lo = 1, int skip_hi = 0);
 void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                    cudaStream_t st, int kskip = 0);
 void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,

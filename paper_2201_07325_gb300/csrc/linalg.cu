@@ -508,13 +508,13 @@ __global__ void __launch_bounds__(256) k_gemm_xrr(LevelDev L, int b0, int kskip)
   gemm_tile<false, false>(g, tm, tn, e);
 }
 
-__global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0) {
+__global__ void __launch_bounds__(512) k_xrr_inverse(LevelDev L, int b0, int skip_lo, int skip_hi) {
   extern __shared__ int ipiv[];
   int b = b0 + blockIdx.x;
   const BoxDesc d = L.desc[b];
   const BoxRun run = L.run[b];
   int r = run.r;
-  if (r == 0) return;
+  if (r == 0 || (r >= skip_lo && r <= skip_hi)) return;   // refined on the tensor cores
   gauss_jordan(L.arena + d.Xinv_off, r, d.a, ipiv, L.status);
 }
 
@@ -524,9 +524,39 @@ void launch_gemm_xrr(const LevelDev& L, int b0, int nb, int amax, cudaStream_t s
                k_gemm_xrr<<<dim3(tiles(amax, amax), nb), 256, 0, st>>>(L, b0, kskip));
 }
 
-void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st) {
+void launch_xrr_inverse(const LevelDev& L, int b0, int nb, int amax, cudaStream_t st,
+                        int skip_lo, int skip_hi) {
   if (nb <= 0) return;
-  FMMLU_LAUNCH("xrr_inverse", st, k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0));
+  FMMLU_LAUNCH("xrr_inverse", st,
+               k_xrr_inverse<<<nb, 512, (size_t)amax * sizeof(int), st>>>(L, b0, skip_lo, skip_hi));
+}
+
+// Boxes refined by Newton-Schulz whose residual max |I - X_RR X_1| exceeds thr
+// (the second iterate's error is about its square) are inverted again in
+// fp64 from the stored copy of X_RR.
+__global__ void __launch_bounds__(512) k_ns_fallback(LevelDev L, int b0,
+                                                     const TcUnit* __restrict__ units, double thr) {
+  extern __shared__ int ipiv[];
+  const int b = b0 + units[blockIdx.x].box;
+  const BoxDesc d = L.desc[b];
+  const int r = L.run[b].r;
+  const double err = __longlong_as_double((long long)L.ns_err[b]);
+  if (r == 0 || err <= thr) return;
+  double2* X = L.arena + d.Xinv_off;
+  const double2* A = L.nsbuf + L.ns_off[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)r * r; e += blockDim.x) {
+    const int i = (int)(e % r), c = (int)(e / r);
+    X[i + (int64_t)c * d.a] = A[i + (int64_t)c * d.a];
+  }
+  __syncthreads();
+  gauss_jordan(X, r, d.a, ipiv, L.status);
+}
+
+void launch_ns_fallback(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, int amax,
+                        double thr, cudaStream_t st) {
+  if (nunits <= 0) return;
+  FMMLU_LAUNCH("xrr_fallback", st,
+               k_ns_fallback<<<nunits, 512, (size_t)amax * sizeof(int), st>>>(L, b0, d_units, thr));
 }
 
 // ---------------------------------------------------------------------------

@@ -305,6 +305,56 @@ struct TcXrr {      // X_RR = A_RR - A_RS T (before inversion): r x r x s
   }
 };
 
+// Newton-Schulz refinement of X ~ X_RR^{-1} (boxes kNsMin <= r <= ns_rmax):
+// Y = X_RR X into the box's product scratch (recording max |I - Y|), then
+// X <- 2 X - X Y in place (the operands were split before the product runs).
+__device__ __forceinline__ bool ns_box(const LevelDev& L, const BoxRun& rr) {
+  return rr.r >= kNsMin && rr.r <= L.ns_rmax;
+}
+struct TcNsY {
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, rr);
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    const int b = (int)(&d - L.desc);
+    return L.nsbuf[L.ns_off[b] + i + (int64_t)kk * d.a];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.arena[d.Xinv_off + kk + (int64_t)j * d.a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const int b = (int)(&d - L.desc);
+    const int64_t a = d.a;
+    L.nsbuf[L.ns_off[b] + a * a + i + j * a] = make_double2(vr, vi);
+    const double e = fmax(fabs(vr - (i == j ? 1.0 : 0.0)), fabs(vi));
+    atomicMax(&L.ns_err[b], (unsigned long long)__double_as_longlong(e));
+  }
+};
+struct TcNsX {
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+                              int& k) {
+    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, rr);
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    return L.arena[d.Xinv_off + i + (int64_t)kk * d.a];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    const int b = (int)(&d - L.desc);
+    const int64_t a = d.a;
+    return L.nsbuf[L.ns_off[b] + a * a + kk + (int64_t)j * a];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    double2* x = L.arena + d.Xinv_off + i + (int64_t)j * d.a;
+    const double2 o = *x;
+    *x = make_double2(2.0 * o.x - vr, 2.0 * o.y - vi);
+  }
+};
+
 // G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
 template <typename CM>
 struct TcGram {
@@ -726,6 +776,8 @@ static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) 
     case kTcSchur: m = z.s + z.n; n = m; k = z.r; return z.r >= kTcInnerMin;
     case kTcXrr: m = z.r; n = z.r; k = z.s; return z.r > 0 && z.s >= kTcInnerMin;
     case kTcGram: m = z.a; n = z.a; k = z.kgram; return z.a > 0;
+    case kTcNsY:
+    case kTcNsX: m = z.r; n = z.r; k = z.r; return z.r >= kNsMin && z.r <= z.nsmax;
   }
   return false;
 }
@@ -813,6 +865,8 @@ void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_
     case kTcW: launch_tc<TcW, 7, 6>("gemm_w_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcSchur: launch_tc<TcSchur, 7, 6>("schur_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcXrr: launch_tc<TcXrr, 7, 6>("gemm_xrr_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcNsY: launch_tc<TcNsY, 7, 6>("ns_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcNsX: launch_tc<TcNsX, 7, 6>("ns_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcGram:
       if (fp32) launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
       else launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
