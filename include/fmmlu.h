@@ -106,6 +106,14 @@ typedef struct fmmlu_opts {
   int id_method;              /* FMMLU_ID_*: how the ID of Def. ID picks its
                                  skeleton (the same greedy column selection
                                  either way). Default FMMLU_ID_AUTO.        */
+  double xrr_refine_tol;      /* schur_emulation 1 only: X_RR^{-1} of boxes
+                                 with 32 <= r <= 640 is an fp32 inverse plus
+                                 three Newton-Schulz steps on the tensor
+                                 cores; a box whose last residual
+                                 max|I - X_RR X| exceeds this tolerance is
+                                 inverted again in fp64. Default 1e-9; 0
+                                 inverts every such box again; < 0 turns the
+                                 refinement off (fp64 Gauss-Jordan).        */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if

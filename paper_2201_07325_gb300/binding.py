@@ -45,6 +45,7 @@ class fmmlu_opts(ctypes.Structure):
         ("cpqr_single", ctypes.c_int),
         ("schur_emulation", ctypes.c_int),
         ("id_method", ctypes.c_int),
+        ("xrr_refine_tol", ctypes.c_double),
     ]
 
 

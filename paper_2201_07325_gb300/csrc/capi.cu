@@ -158,6 +158,7 @@ void default_opts(fmmlu_opts* o) {
   o->cpqr_single = 0;
   o->schur_emulation = 1;
   o->id_method = FMMLU_ID_AUTO;
+  o->xrr_refine_tol = 1e-9;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -172,6 +173,7 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (!(o.eps_id_divisor > 0.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps_id_divisor must be > 0");
   if (o.id_method < 0 || o.id_method > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad id_method");
   if (o.schur_emulation < 0 || o.schur_emulation > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad schur_emulation");
+  if (std::isnan(o.xrr_refine_tol)) throw Error(FMMLU_ERR_INVALID_ARG, "xrr_refine_tol is NaN");
   return o;
 }
 
@@ -526,7 +528,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     // refinement of X_RR^{-1} (tcgen05 path): per colour an X_RR copy and a
     // product scratch of a^2 each per box
     int ns_rmax = 0;
-    if (opt.schur_emulation == 1) {   // the tcgen05 path
+    if (opt.schur_emulation == 1 && opt.xrr_refine_tol >= 0.0) {   // the tcgen05 path
       for (int r = kNsMin; r <= 4096; r += 8)
         if (gj32_cluster_size(r) > 0) ns_rmax = r; else break;
     }
@@ -853,7 +855,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           CK(cudaMemsetAsync(LD.ns_err + b0, 0, (size_t)cnt * sizeof(unsigned long long), st));
           ns(kTcNsY);
           ns(kTcNsX);
-          launch_ns_fallback(LD, b0, elim_units.d + ns_off0, ns_cnt, amax, 1e-9, st);
+          launch_ns_fallback(LD, b0, elim_units.d + ns_off0, ns_cnt, amax, opt.xrr_refine_tol, st);
           ns_done = true;
         } else if (eg != cudaErrorNotSupported) {
           CK(eg);
@@ -1032,7 +1034,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         std::memcpy(&v, &errs[e], sizeof(v));
         ++ns_boxes;
         ns_worst = std::max(ns_worst, v);
-        if (!(v <= 1e-9)) ++ns_fallback;
+        if (!(v <= opt.xrr_refine_tol)) ++ns_fallback;
       }
     }
     if (opt.verbose)
@@ -1043,7 +1045,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     js << (first_level ? "" : ", ") << "{\"level\": " << lev << ", \"boxes\": " << nb
        << ", \"colours\": " << HL.ncolours << ", \"current\": " << L->cur.size()
        << ", \"sum_a\": " << sum_a << ", \"sum_s\": " << sum_s << ", \"max_a\": " << max_a
-       << ", \"max_r\": " << max_r << ", \"ms\": " << lms << "}";
+       << ", \"max_r\": " << max_r << ", \"refined_inverses\": " << ns_boxes
+       << ", \"refine_fallbacks\": " << ns_fallback << ", \"ms\": " << lms << "}";
     first_level = false;
     prev = std::move(L);
   }

@@ -198,6 +198,36 @@ def test_gram_id_matches_householder_id(pkg, ell, prec):
     assert abs(out["householder"]["n0"] - out["gram"]["n0"]) <= max(4, 0.02 * out["gram"]["n0"])
 
 
+@pytest.mark.parametrize("tol", [-1.0, 0.0, 1e-9])
+def test_xrr_inverse_refinement_and_fallback(pkg, ell, tol):
+    """X_RR^{-1} by an fp32 inverse plus Newton-Schulz steps on the tensor cores
+    (tol 1e-9, the default), with every refined box inverted again in fp64
+    (tol 0: the fallback path), and by fp64 Gauss-Jordan alone (tol < 0): each
+    reproduces the dense LU at eps = 1e-14 and they agree far below eps = 1e-6."""
+    s, A, b, xd = ell
+    fac = _gpu_factor(pkg, s, K, 1e-14, leaf_size=24, precision=pkg.PRECISION_FP64,
+                      xrr_refine_tol=tol)
+    x = fac.solve(torch.from_numpy(b)).cpu().numpy()
+    fac.free()
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 1e-10
+    xs = {}
+    for t in sorted({-1.0, tol}):
+        fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          xrr_refine_tol=t)
+        xs[t] = fac.solve(torch.from_numpy(b)).cpu().numpy()
+        st = fac.stats()
+        fac.free()
+        refined = sum(l["refined_inverses"] for l in st["levels"])
+        fallbacks = sum(l["refine_fallbacks"] for l in st["levels"])
+        if t < 0:
+            assert refined == 0
+        else:
+            assert refined > 0
+            assert fallbacks == (refined if t == 0.0 else 0)
+    assert np.linalg.norm(A @ xs[tol] - b) / np.linalg.norm(b) <= 1e-5
+    assert np.linalg.norm(xs[tol] - xs[-1.0]) / np.linalg.norm(xs[-1.0]) <= 1e-8
+
+
 def test_single_box_is_dense_lu(pkg):
     s = synth.ellipsoid_uniform(50, seed=3)
     A = kernel.dense_matrix(s.points, s.normals, s.weights, 3.0, 3.0)
