@@ -402,9 +402,8 @@ __device__ __forceinline__ int tc_exponent(double mx) {
 }
 
 template <class Prob, bool SideB>
-__global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-                                                int* expo, const TcUnit* __restrict__ units) {
-  const TcUnit u = units[blockIdx.x];
+__device__ __forceinline__ void tc_exp_unit(const LevelDev& L, int b0, const TcBoxHost* __restrict__ tb,
+                                            int* expo, const TcUnit& u) {
   const int b = b0 + u.box;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
@@ -450,14 +449,23 @@ __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxH
   }
 }
 
+// one launch for both operands: the unit says which side
+template <class Prob>
+__global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+                                                int* expo, const TcUnit* __restrict__ units) {
+  const TcUnit u = units[blockIdx.x];
+  if (u.side) tc_exp_unit<Prob, true>(L, b0, tb, expo, u);
+  else tc_exp_unit<Prob, false>(L, b0, tb, expo, u);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) { return tc::bf16_pair(lo, hi); }
 
 // grid: x = 32-row groups, y = k-octet groups of 8 (one per warp), z = boxes
 template <class Prob, int NS, bool SideB>
-__global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
-                                                   unsigned char* slices, const int* __restrict__ expo,
-                                                   const TcUnit* __restrict__ units) {
-  const TcUnit u = units[blockIdx.x];
+__device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
+                                               const TcBoxHost* __restrict__ tb,
+                                               unsigned char* slices, const int* __restrict__ expo,
+                                               const TcUnit& u) {
   const int b = b0 + u.box;
   const BoxDesc& d = L.desc[b];
   const BoxRun rr = L.run[b];
@@ -524,6 +532,15 @@ __global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcB
       }
     }
   }
+}
+
+template <class Prob, int NS>
+__global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcBoxHost* __restrict__ tb,
+                                                   unsigned char* slices, const int* __restrict__ expo,
+                                                   const TcUnit* __restrict__ units) {
+  const TcUnit u = units[blockIdx.x];
+  if (u.side) tc_digits_unit<Prob, NS, true>(L, b0, tb, slices, expo, u);
+  else tc_digits_unit<Prob, NS, false>(L, b0, tb, slices, expo, u);
 }
 
 // ---------------------------------------------------------------------------
@@ -821,20 +838,14 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, const TcBoxHo
                       void* slices, int* expo, const TcExtra& x, const TcUnit* d_units,
                       const TcPlan& pl, cudaStream_t st) {
   unsigned char* sl = reinterpret_cast<unsigned char*>(slices);
-  if (pl.cnt[0] > 0)
+  // the exponent units of both sides are adjacent in the list, so are the digit units
+  const int ne = pl.cnt[0] + pl.cnt[1], nd = pl.cnt[2] + pl.cnt[3];
+  if (ne > 0)
     FMMLU_LAUNCH("tc_split", st,
-                 (k_tc_exp<Prob, false><<<pl.cnt[0], 256, 0, st>>>(L, b0, d_tb, expo, d_units + pl.off[0])));
-  if (pl.cnt[1] > 0)
+                 (k_tc_exp<Prob><<<ne, 256, 0, st>>>(L, b0, d_tb, expo, d_units + pl.off[0])));
+  if (nd > 0)
     FMMLU_LAUNCH("tc_split", st,
-                 (k_tc_exp<Prob, true><<<pl.cnt[1], 256, 0, st>>>(L, b0, d_tb, expo, d_units + pl.off[1])));
-  if (pl.cnt[2] > 0)
-    FMMLU_LAUNCH("tc_split", st,
-                 (k_tc_digits<Prob, NS, false><<<pl.cnt[2], 256, 0, st>>>(L, b0, d_tb, sl, expo,
-                                                                          d_units + pl.off[2])));
-  if (pl.cnt[3] > 0)
-    FMMLU_LAUNCH("tc_split", st,
-                 (k_tc_digits<Prob, NS, true><<<pl.cnt[3], 256, 0, st>>>(L, b0, d_tb, sl, expo,
-                                                                         d_units + pl.off[3])));
+                 (k_tc_digits<Prob, NS><<<nd, 256, 0, st>>>(L, b0, d_tb, sl, expo, d_units + pl.off[2])));
   if (pl.cnt[4] <= 0) return;
   const size_t smem = tc_smem_bytes(NS);
   static bool attr = false;
