@@ -1078,7 +1078,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     launch_assemble_root(g, H->d_root_dofs, d_owner, d_pos, d_pairoff, R->d_cur_a0, nc, R->d_pool,
                          n0, H->d_root, st);
     double2* wk = rw.get<double2>((size_t)n0 * H->nb_root);
-    launch_root_factor(H->d_root, n0, H->nb_root, wk, d_status, st);
+    CK(launch_root_factor(H->d_root, n0, H->nb_root, wk, d_status, st, opt.schur_emulation == 1));
     CK(cudaGetLastError());
     int status = ddownload(d_status, 1, st)[0];
     std::string msg;
@@ -1090,8 +1090,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
         H->prof.add_work("root_diag", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
         if (later > 0) {
-          H->prof.add_work("root_w", 8.0 * later * r_ * r_, 16.0 * (2 * later * r_ + r_ * r_));
-          H->prof.add_work("root_schur", 8.0 * later * later * r_,
+          const bool tcr = opt.schur_emulation == 1 && r_ >= kTcInnerMin;
+          const double c = tcr ? 28.0 * 4.0 * 2.0 : 8.0;
+          H->prof.add_work(tcr ? "root_w_tc" : "root_w", c * later * r_ * r_,
+                           16.0 * (2 * later * r_ + r_ * r_));
+          H->prof.add_work(tcr ? "root_schur_tc" : "root_schur", c * later * later * r_,
                            16.0 * (2 * later * later + 2 * later * r_));
         }
         rb += 1;

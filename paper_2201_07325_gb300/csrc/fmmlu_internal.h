@@ -94,6 +94,11 @@ struct LevelDev {   // device state of a level
   const int64_t* ns_off;
   unsigned long long* ns_err;   // max |I - X_RR X_1| per box, as double bits
   int ns_rmax;
+  // root block elimination on the tensor cores (one step: block [i0, i0 + r))
+  double2* root_A;   // n0 x n0, ld n0
+  double2* root_W;   // later x r, ld later
+  int64_t root_n0;
+  int root_i0, root_r;
 };
 constexpr int kNsMin = 32;      // smallest r refined on the tensor cores
 
@@ -230,7 +235,7 @@ void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_
 size_t tc_smem_bytes(int ns);
 // problems of the tcgen05 path
 enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5, kTcNsY = 6,
-       kTcNsX = 7 };
+       kTcNsX = 7, kTcRootW = 8, kTcRootS = 9 };
 struct TcUnit {          // one CTA of a tcgen05-path launch
   int box;               // box index relative to the colour's first box
   int side;              // 0 = A operand, 1 = B operand (split launches)
@@ -276,8 +281,11 @@ void launch_gemm_w(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                    cudaStream_t st, int kskip = 0);
 void launch_schur_update(const LevelDev& L, int b0, int nb, int amax, int nmax_max,
                          cudaStream_t st, int kskip = 0);
-void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
-                        cudaStream_t st);
+cudaError_t launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
+                               cudaStream_t st, bool tensor_cores = false);
+void launch_root_diag(double2* A, int n0, int i0, int r, int* status, cudaStream_t st);
+cudaError_t launch_root_factor_tc(double2* A, int n0, int nb, double2* W, int* status,
+                                  cudaStream_t st);
 // solve.cu
 void launch_gather_vec(const double2* b, const int* perm, int64_t n, int nrhs,
                        double2* v, cudaStream_t st);

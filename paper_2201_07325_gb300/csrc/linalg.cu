@@ -590,8 +590,13 @@ __global__ void __launch_bounds__(256) k_root_schur(double2* A, int64_t n0, int 
   gemm_tile<false, false>(g, tm, tn, e);
 }
 
-void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
-                        cudaStream_t st) {
+void launch_root_diag(double2* A, int n0, int i0, int r, int* status, cudaStream_t st) {
+  FMMLU_LAUNCH("root_diag", st, k_root_diag<<<1, 512, 0, st>>>(A, n0, i0, r, status));
+}
+
+cudaError_t launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
+                               cudaStream_t st, bool tensor_cores) {
+  if (tensor_cores) return launch_root_factor_tc(A, n0, nb, work, status, st);
   for (int i0 = 0; i0 < n0; i0 += nb) {
     int r = std::min(nb, n0 - i0);
     FMMLU_LAUNCH("root_diag", st, k_root_diag<<<1, 512, 0, st>>>(A, n0, i0, r, status));
@@ -602,6 +607,7 @@ void launch_root_factor(double2* A, int n0, int nb, double2* work, int* status,
                    k_root_schur<<<tiles(later, later), 256, 0, st>>>(A, n0, i0, r, work));
     }
   }
+  return cudaGetLastError();
 }
 
 }  // namespace fmmlu

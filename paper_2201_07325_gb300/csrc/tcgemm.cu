@@ -355,6 +355,51 @@ struct TcNsX {
   }
 };
 
+// Root block elimination, step [i0, i1 = i0 + r), later = n0 - i1:
+// W = A[later, i0:i1] D^{-1} (D^{-1} in the diagonal block), then
+// A[later, later] -= W A[i0:i1, later]. The level and box arguments are unused.
+struct TcRootW {
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun&, int& m, int& n,
+                              int& k) {
+    m = (int)(L.root_n0 - L.root_i0 - L.root_r); n = L.root_r; k = L.root_r;
+    return m > 0 && k >= kTcInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc&, const BoxRun&, int i, int kk) {
+    return L.root_A[(L.root_i0 + L.root_r + i) + (int64_t)(L.root_i0 + kk) * L.root_n0];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc&, const BoxRun&, int kk, int j) {
+    return L.root_A[(L.root_i0 + kk) + (int64_t)(L.root_i0 + j) * L.root_n0];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc&, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const int64_t later = L.root_n0 - L.root_i0 - L.root_r;
+    L.root_W[i + j * later] = make_double2(vr, vi);
+  }
+};
+struct TcRootS {
+  static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun&, int& m, int& n,
+                              int& k) {
+    m = (int)(L.root_n0 - L.root_i0 - L.root_r); n = m; k = L.root_r;
+    return m > 0 && k >= kTcInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc&, const BoxRun&, int i, int kk) {
+    const int64_t later = L.root_n0 - L.root_i0 - L.root_r;
+    return L.root_W[i + kk * later];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc&, const BoxRun&, int kk, int j) {
+    return L.root_A[(L.root_i0 + kk) + (int64_t)(L.root_i0 + L.root_r + j) * L.root_n0];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc&, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const int64_t i1 = L.root_i0 + L.root_r;
+    double2* x = L.root_A + (i1 + i) + (i1 + j) * L.root_n0;
+    const double2 o = *x;
+    *x = make_double2(o.x - vr, o.y - vi);
+  }
+};
+
 // G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
 template <typename CM>
 struct TcGram {
@@ -795,6 +840,9 @@ static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) 
     case kTcGram: m = z.a; n = z.a; k = z.kgram; return z.a > 0;
     case kTcNsY:
     case kTcNsX: m = z.r; n = z.r; k = z.r; return z.r >= kNsMin && z.r <= z.nsmax;
+    // root step: a = later DOFs, r = block width
+    case kTcRootW: m = z.a; n = z.r; k = z.r; return z.a > 0 && z.r >= kTcInnerMin;
+    case kTcRootS: m = z.a; n = z.a; k = z.r; return z.a > 0 && z.r >= kTcInnerMin;
   }
   return false;
 }
@@ -878,11 +926,83 @@ void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_
     case kTcXrr: launch_tc<TcXrr, 7, 6>("gemm_xrr_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcNsY: launch_tc<TcNsY, 7, 6>("ns_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcNsX: launch_tc<TcNsX, 7, 6>("ns_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcRootW: launch_tc<TcRootW, 7, 6>("root_w_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcRootS: launch_tc<TcRootS, 7, 6>("root_schur_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcGram:
       if (fp32) launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
       else launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
       break;
   }
+}
+
+// ---------------------------------------------------------------------------
+// the root factor with its two products per step on the tensor cores: the
+// diagonal-block inverses stay fp64 Gauss-Jordan (launch_root_diag); all
+// steps' unit lists are known up front and uploaded once.
+
+cudaError_t launch_root_factor_tc(double2* A, int n0, int nb, double2* W, int* status,
+                                  cudaStream_t st) {
+  struct Step { int i0, r; TcPlan pw, ps; };
+  std::vector<Step> steps;
+  std::vector<TcUnit> units;
+  for (int i0 = 0; i0 < n0; i0 += nb) {
+    Step sp;
+    sp.i0 = i0;
+    sp.r = std::min(nb, n0 - i0);
+    const std::vector<TcBoxSize> bs{TcBoxSize{n0 - i0 - sp.r, 0, sp.r, 0, 0, 0}};
+    tc_plan(kTcRootW, bs, units, sp.pw);
+    tc_plan(kTcRootS, bs, units, sp.ps);
+    steps.push_back(sp);
+  }
+  int64_t so = 0, eo = 0;
+  TcBoxHost tb;
+  plan_tc_box(n0, n0, nb, 7, so, eo, tb);
+  void *d_slices = nullptr, *d_expo = nullptr, *d_units = nullptr, *d_tb = nullptr,
+       *d_desc = nullptr, *d_run = nullptr;
+  auto cleanup = [&]() {
+    for (void* p : {d_slices, d_expo, d_units, d_tb, d_desc, d_run}) if (p) cudaFree(p);
+  };
+  cudaError_t err = cudaSuccess;
+  auto ck = [&](cudaError_t e) {
+    if (err == cudaSuccess && e != cudaSuccess) err = e;
+    return err == cudaSuccess;
+  };
+  if (!(ck(cudaMalloc(&d_slices, (size_t)std::max<int64_t>(so, 16))) &&
+        ck(cudaMalloc(&d_expo, (size_t)std::max<int64_t>(eo, 1) * sizeof(int))) &&
+        ck(cudaMalloc(&d_units, std::max<size_t>(units.size(), 1) * sizeof(TcUnit))) &&
+        ck(cudaMalloc(&d_tb, sizeof(TcBoxHost))) && ck(cudaMalloc(&d_desc, sizeof(BoxDesc))) &&
+        ck(cudaMalloc(&d_run, sizeof(BoxRun))) &&
+        ck(cudaMemsetAsync(d_desc, 0, sizeof(BoxDesc), st)) &&
+        ck(cudaMemsetAsync(d_run, 0, sizeof(BoxRun), st)) &&
+        ck(cudaMemcpyAsync(d_tb, &tb, sizeof(TcBoxHost), cudaMemcpyHostToDevice, st)) &&
+        (units.empty() || ck(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(TcUnit),
+                                             cudaMemcpyHostToDevice, st))))) {
+    cudaStreamSynchronize(st);
+    cleanup();
+    return err;
+  }
+  LevelDev L{};
+  L.desc = reinterpret_cast<const BoxDesc*>(d_desc);
+  L.run = reinterpret_cast<BoxRun*>(d_run);
+  L.status = status;
+  L.root_A = A;
+  L.root_W = W;
+  L.root_n0 = n0;
+  const TcUnit* du = reinterpret_cast<const TcUnit*>(d_units);
+  for (const Step& sp : steps) {
+    launch_root_diag(A, n0, sp.i0, sp.r, status, st);
+    if (n0 - sp.i0 - sp.r <= 0) continue;
+    L.root_i0 = sp.i0;
+    L.root_r = sp.r;
+    launch_tc_planned(kTcRootW, L, 0, reinterpret_cast<const TcBoxHost*>(d_tb), d_slices,
+                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.pw, st);
+    launch_tc_planned(kTcRootS, L, 0, reinterpret_cast<const TcBoxHost*>(d_tb), d_slices,
+                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.ps, st);
+  }
+  ck(cudaGetLastError());
+  ck(cudaStreamSynchronize(st));   // the buffers above are freed next
+  cleanup();
+  return err;
 }
 
 }  // namespace fmmlu
