@@ -437,6 +437,14 @@ __device__ __forceinline__ double2 tc_elem(const LevelDev& L, const BoxDesc& d, 
   return side_b ? Prob::B(L, d, rr, kk, row) : Prob::A(L, d, rr, row, kk);
 }
 
+// largest component magnitude as the bit pattern of a non-negative double:
+// integer max on the magnitude bits orders like the values (NaN above inf)
+__device__ __forceinline__ unsigned long long mag_bits(double2 v) {
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long ay = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
+  return ax > ay ? ax : ay;
+}
+
 __device__ __forceinline__ int tc_exponent(double mx) {
   int e = 0;
   if (mx > 0.0) {
@@ -465,32 +473,43 @@ __device__ __forceinline__ void tc_exp_unit(const LevelDev& L, int b0, const TcB
   if (kcontig) {                 // a warp per row, lanes along k
     const int row = u.x * 8 + (threadIdx.x >> 5);
     if (row >= lpad) return;
-    double mx = 0.0;
+    unsigned long long mb = 0;
     if (row < len)
       for (int kk = lane; kk < k; kk += 32) {
-        const double2 v = tc_elem<Prob>(L, d, rr, side_b, row, kk);
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        const unsigned long long q = mag_bits(tc_elem<Prob>(L, d, rr, side_b, row, kk));
+        mb = q > mb ? q : mb;
       }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long q = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = q > mb ? q : mb;
+    }
+    double mx = __longlong_as_double((long long)mb);
     if (!(mx <= 1.7976931348623157e308)) {
       if (lane == 0) set_status(L.status, kStatusNonfinite);
       mx = 0.0;
     }
     if (lane == 0) ex[row] = tc_exponent(mx);
-  } else {                       // a thread per row, consecutive rows contiguous
-    const int row = u.x * 256 + threadIdx.x;
-    if (row >= lpad) return;
-    double mx = 0.0;
+  } else {                       // 32 consecutive rows per block, k split over the 8 warps
+    __shared__ unsigned long long s_mx[8][32];
+    const int warp = threadIdx.x >> 5;
+    const int row = u.x * 32 + lane;
+    unsigned long long mb = 0;
     if (row < len)
-      for (int kk = 0; kk < k; ++kk) {
-        const double2 v = tc_elem<Prob>(L, d, rr, side_b, row, kk);
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      for (int kk = warp; kk < k; kk += 8) {
+        const unsigned long long q = mag_bits(tc_elem<Prob>(L, d, rr, side_b, row, kk));
+        mb = q > mb ? q : mb;
       }
-    if (!(mx <= 1.7976931348623157e308)) {
-      set_status(L.status, kStatusNonfinite);
-      mx = 0.0;
+    s_mx[warp][lane] = mb;
+    __syncthreads();
+    if (warp == 0) {
+      for (int w = 1; w < 8; ++w) mb = s_mx[w][lane] > mb ? s_mx[w][lane] : mb;
+      double mx = __longlong_as_double((long long)mb);
+      if (!(mx <= 1.7976931348623157e308)) {
+        set_status(L.status, kStatusNonfinite);
+        mx = 0.0;
+      }
+      if (row < lpad) ex[row] = tc_exponent(mx);
     }
-    ex[row] = tc_exponent(mx);
   }
 }
 
@@ -532,8 +551,10 @@ __device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
     const int kk = 8 * ko + u;
     double2 v = make_double2(0.0, 0.0);
     if (row < len && kk < k) v = tc_elem<Prob>(L, d, rr, SideB, row, kk);
-    if (!(fabs(v.x) <= 1.7976931348623157e308 && fabs(v.y) <= 1.7976931348623157e308))
-      v = make_double2(0.0, 0.0);   // reported by the exponent pass
+    if (mag_bits(v) >= 0x7FF0000000000000ull) {   // inf or NaN (exponent bits all set)
+      set_status(L.status, kStatusNonfinite);   // NaN escapes the exponent pass's fmax
+      v = make_double2(0.0, 0.0);
+    }
     tc::balanced_digits<NS>(v.x, e, cr[u]);
     tc::balanced_digits<NS>(v.y, e, ci[u]);
   }
@@ -787,10 +808,19 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           const int j = T.j0 + 16 * half + c;
           if (j >= T.n) continue;
           const int E = ei + expo[t.eb_off + j];
-          const double vr =
-              ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
-          const double vi =
-              ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
+          // value = X_hi 2^(E - 32) + X_lo 2^(E - 16 - 8 DMAX); the powers of two
+          // are built from their bits (GB300's fp64 pipe is the scarce unit)
+          const int bh = E - 32 + 1023, bl = E - 16 - 8 * DMAX + 1023;
+          double vr, vi;
+          if (bl >= 1 && bh <= 2046) {
+            const double sh = __longlong_as_double((long long)bh << 52);
+            const double sl = __longlong_as_double((long long)bl << 52);
+            vr = fma((double)xl[c][0], sl, (double)xh[c][0] * sh);
+            vi = fma((double)xl[c][1], sl, (double)xh[c][1] * sh);
+          } else {
+            vr = ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
+            vi = ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
+          }
           Prob::epi(L, d, rr, x, i, j, vr, vi);
         }
       }
@@ -862,7 +892,7 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
       const int kg = (2 * ((k + 15) / 16) + 7) / 8;
       if (l < 2) {                       // exponents of side A / B
         const int lp = l == 0 ? lpa : lpb;
-        const int per = tc_kcontig(which, l == 1) ? 8 : 256;
+        const int per = tc_kcontig(which, l == 1) ? 8 : 32;
         for (int x = 0; x < (lp + per - 1) / per; ++x) units.push_back(TcUnit{e, l, x, 0});
       } else if (l < 4) {                // digits of side A / B
         const int lp = l == 2 ? lpa : lpb;
