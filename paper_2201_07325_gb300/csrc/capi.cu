@@ -647,7 +647,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       gj_scratch = std::max(gj_scratch, off);
     }
     // Gram form of the ID: per colour digit slices, exponents and G/R blocks;
-    // pivoted-Cholesky CTAs in proportion to a^3 with >= 16 columns per CTA,
+    // pivoted-Cholesky CTAs in proportion to a^3 with >= 8 columns per CTA,
     // co-resident (cooperative) when the colour fits, else one CTA per box.
     // G = M^H M on tcgen05 (default) or on the mma.sync path (schur_emulation 2)
     const bool gram_tc = opt.schur_emulation != 2;
@@ -681,7 +681,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           tot = 0;
           for (int e = 0; e < cnt; ++e) {
             const int a = desc[b0 + e].a;
-            const int pmax = std::max(1, (a + 15) / 16);   // >= 16 columns per CTA
+            const int pmax = std::max(1, (a + 7) / 8);   // >= 8 columns per CTA
             P[e] = std::max(1, std::min(pmax, (int)std::floor(cap * std::pow((double)a, 3.0) /
                                                               std::max(wsum, 1.0))));
             tot += P[e];
