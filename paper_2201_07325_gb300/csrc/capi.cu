@@ -709,6 +709,21 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) gram_box[e] = gram_col[sgi];
     GramBoxHost* d_gbh = use_gram ? lw.up(gbh, st) : nullptr;
     TcBoxHost* d_gtb = use_gram && gram_tc ? lw.up(gtb, st) : nullptr;
+    // split-K accumulator of the Gram products: 4 int64 per entry of each box's G
+    std::vector<int64_t> gx_off(nb, 0), gx_col_off(seg_start.size(), 0), gx_col_len(seg_start.size(), 0);
+    int64_t gx_max = 1;
+    if (use_gram && gram_tc)
+      for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
+        int64_t o = 0;
+        for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
+          gx_off[e] = o;
+          o += 4 * (int64_t)desc[e].a * desc[e].a;
+        }
+        gx_col_len[sgi] = o;
+        gx_max = std::max(gx_max, o);
+      }
+    unsigned long long* d_gx = use_gram && gram_tc ? lw.get<unsigned long long>((size_t)gx_max) : nullptr;
+    const int64_t* d_gx_off = use_gram && gram_tc ? lw.up(gx_off, st) : nullptr;
     void* d_gr_slices = use_gram ? (void*)lw.get<unsigned char>((size_t)gr_slices) : nullptr;
     int* d_gr_expo = use_gram ? lw.get<int>((size_t)gr_expo) : nullptr;
     double2* d_gr_g = use_gram ? lw.get<double2>((size_t)gr_g) : nullptr;
@@ -763,15 +778,22 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
       if (gram_col[sgi]) {
         if (gram_tc) {
-          // Gram tiles from a (exact); the k range from the row bound m_max
+          // Gram tiles from a (exact); the k range (split into chunks whose
+          // exact int64 sums add up in gx) from the row bound m_max
           std::vector<TcBoxSize> bs(cnt);
           for (int e = 0; e < cnt; ++e) bs[e] = TcBoxSize{desc[b0 + e].a, 0, 0, 0, desc[b0 + e].mmax};
           std::vector<TcUnit> units;
           TcPlan pl;
           tc_plan(kTcGram, bs, units, pl);
+          const int fin0 = (int)units.size();
+          for (int e = 0; e < cnt; ++e) units.push_back(TcUnit{e, 0, 0, 0});
           gram_units.upload(units, st);
+          CK(cudaMemsetAsync(d_gx + gx_col_off[sgi], 0,
+                             (size_t)gx_col_len[sgi] * sizeof(unsigned long long), st));
           launch_tc_planned(kTcGram, LD, b0, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g,
-                            H->fp32, gram_units.d, pl, st);
+                            H->fp32, gram_units.d, pl, st, d_gx, d_gx_off);
+          launch_gram_finalize(LD, b0, gram_units.d + fin0, cnt, amax, d_gtb + b0, d_gr_expo, d_gbh,
+                               d_gr_g, d_gx, d_gx_off, H->fp32, st);
         } else
           launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
         CK(cudaGetLastError());

@@ -170,13 +170,14 @@ __device__ __forceinline__ void comb_kernel_pair(R dx, R dy, R dz,   // s - t
                                                  typename CT<R>::T& kst, typename CT<R>::T& g) {
   const R r2 = dx * dx + dy * dy + dz * dz;
   const R r = sqrt(r2);
+  const R inv_r2 = R(1) / r2;     // the one division: 1/r = r / r^2
   R sn, cs;
   sincos(k * r, &sn, &cs);
-  const R ginv = R(1) / (R(4 * kPi) * r);
+  const R ginv = (r * inv_r2) * R(1.0 / (4.0 * kPi));
   g = mk(cs * ginv, sn * ginv);
   const typename CT<R>::T gf = cmul(g, mk(R(-1), k * r));   // G (i k r - 1)
-  const R pts = (dx * snx + dy * sny + dz * snz) / r2;
-  const R pst = -(dx * tnx + dy * tny + dz * tnz) / r2;
+  const R pts = (dx * snx + dy * sny + dz * snz) * inv_r2;
+  const R pst = -(dx * tnx + dy * tny + dz * tnz) * inv_r2;
   kts = mk(gf.x * pts + eta * g.y, gf.y * pts - eta * g.x);
   kst = mk(gf.x * pst + eta * g.y, gf.y * pst - eta * g.x);
 }

@@ -252,7 +252,14 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
              TcPlan& plan);
 void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
                        int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
-                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st);
+                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st,
+                       unsigned long long* gx = nullptr, const int64_t* gx_off = nullptr);
+// G of a colour's boxes (units: one per box) from the Gram product's split-K
+// int64 accumulator
+void launch_gram_finalize(const LevelDev& L, int b0, const TcUnit* d_boxes, int nboxes, int amax,
+                          const TcBoxHost* d_tb, const int* expo, const GramBoxHost* d_gb,
+                          double2* gbuf, unsigned long long* gx, const int64_t* gx_off, bool fp32,
+                          cudaStream_t st);
 // gj_dist.cu: fp32 Gauss-Jordan of X_RR over a thread-block cluster per box
 // (units: one per box, TcUnit::box relative to b0); writes the fp32 inverse to
 // Xinv (as complex128) and a complex128 copy of X_RR to nsbuf

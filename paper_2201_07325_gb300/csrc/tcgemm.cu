@@ -194,7 +194,14 @@ __device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
 struct TcExtra {
   const GramBoxHost* gb;
   double2* gbuf;
+  // split-K products: per box (descriptor index) the offset of its int64
+  // accumulator (4 per entry: hi re, hi im, lo re, lo im)
+  unsigned long long* gx;
+  const int64_t* gx_off;
 };
+
+// k16 steps per chunk of a split-K problem (0: no split)
+template <class Prob> struct TcSplit { static constexpr int steps = 0; };
 
 // kAk / kBk: consecutive k of one row of A / column of B are contiguous in memory
 struct TcSchur {    // Delta(S|N, S|N) -= W X_RC: (s+n) x (s+n) x r
@@ -425,6 +432,36 @@ struct TcGram {
   }
 };
 
+// The Gram matrix's k range (the rows of M, thousands) is split into chunks
+// of 128 k16 steps so that small colours still fill the GPU.
+template <typename CM> struct TcSplit<TcGram<CM>> { static constexpr int steps = 128; };
+
+// G from the split-K int64 accumulator: G_ij = X_hi 2^(E-32) + X_lo 2^(E-16-8 DMAX)
+// for i <= j, mirrored to G_ji = conj(G_ij)
+template <int DMAX>
+__global__ void __launch_bounds__(256) k_gram_finalize(LevelDev L, int b0, const TcUnit* __restrict__ units,
+                                                       const TcBoxHost* __restrict__ tb,
+                                                       const int* __restrict__ expo, TcExtra x) {
+  const TcUnit u = units[blockIdx.y];
+  const int b = b0 + u.box;
+  const BoxDesc& d = L.desc[b];
+  const int64_t a = d.a;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a * a) return;
+  const int i = (int)(e % a), j = (int)(e / a);
+  if (i > j) return;
+  const TcBoxHost t = tb[u.box];
+  const unsigned long long* q = x.gx + x.gx_off[b] + 4 * e;
+  const int E = expo[t.ea_off + i] + expo[t.eb_off + j];
+  const double hr = (double)(long long)q[0], hi = (double)(long long)q[1];
+  const double lr = (double)(long long)q[2], li = (double)(long long)q[3];
+  const double vr = ldexp(hr, E - 32) + ldexp(lr, E - 16 - 8 * DMAX);
+  const double vi = i == j ? 0.0 : ldexp(hi, E - 32) + ldexp(li, E - 16 - 8 * DMAX);
+  double2* G = x.gbuf + x.gb[b].G_off;
+  G[i + j * a] = make_double2(vr, vi);
+  if (i < j) G[j + i * a] = make_double2(vr, -vi);
+}
+
 // ---------------------------------------------------------------------------
 // split: (1) the power-of-two exponent of every row of A (side 0) / column of
 // B (side 1); (2) the digits, each thread converting 8 consecutive k of one
@@ -619,8 +656,11 @@ __global__ void __launch_bounds__(256) k_tc_digits(LevelDev L, int b0, const TcB
 
 struct TcTile {
   bool ok;
-  int rel, b, tm, tn, i0, j0, m, n, KS;
+  int rel, b, tm, tn, i0, j0, m, n;
+  int KSall;   // k16 steps of the whole product
+  int k0, KS;  // this unit's chunk of them (split-K problems), else 0 and KSall
 };
+
 
 template <class Prob>
 __device__ __forceinline__ TcTile tc_tile(const LevelDev& L, int b0, const TcUnit& u) {
@@ -639,7 +679,14 @@ __device__ __forceinline__ TcTile tc_tile(const LevelDev& L, int b0, const TcUni
   if (Prob::kUpper && T.j0 + tc::kCols - 1 < T.i0) return T;   // below the diagonal
   T.m = m;
   T.n = n;
-  T.KS = (k + 15) / 16;
+  T.KSall = (k + 15) / 16;
+  T.k0 = 0;
+  T.KS = T.KSall;
+  if (TcSplit<Prob>::steps > 0) {
+    T.k0 = u.y * TcSplit<Prob>::steps;
+    if (T.k0 >= T.KSall) return T;   // past the end of this box's k range
+    T.KS = min(TcSplit<Prob>::steps, T.KSall - T.k0);
+  }
   T.ok = true;
   return T;
 }
@@ -687,8 +734,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
         if (!T.ok) continue;
         const TcBoxHost t = tb[T.rel];
-        const unsigned char* srcA = slices + t.a_off + (int64_t)T.tm * T.KS * kA;
-        const unsigned char* srcB = slices + t.b_off + (int64_t)T.tn * T.KS * kB;
+        const unsigned char* srcA = slices + t.a_off + ((int64_t)T.tm * T.KSall + T.k0) * kA;
+        const unsigned char* srcB = slices + t.b_off + ((int64_t)T.tn * T.KSall + T.k0) * kB;
         for (int ks = 0; ks < T.KS; ++ks, ++g) {
           const int s = g & 1;
           if (g >= 2 && !mbar_wait(&bar_empty[s], ((g >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
@@ -798,6 +845,24 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       }
       if (!ok || *abort_flag) break;
       const int i = T.i0 + row;
+      if (TcSplit<Prob>::steps > 0) {
+        // add this chunk's exact digit sums into the box's int64 accumulator
+        if (i < T.m) {
+          const BoxDesc& d = L.desc[T.b];
+          unsigned long long* acc = x.gx + x.gx_off[T.b];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = T.j0 + 16 * half + c;
+            if (j >= T.n || (Prob::kUpper && i > j)) continue;
+            unsigned long long* q = acc + 4 * ((int64_t)i + (int64_t)j * d.a);
+            atomicAdd(q + 0, (unsigned long long)xh[c][0]);
+            atomicAdd(q + 1, (unsigned long long)xh[c][1]);
+            atomicAdd(q + 2, (unsigned long long)xl[c][0]);
+            atomicAdd(q + 3, (unsigned long long)xl[c][1]);
+          }
+        }
+        continue;
+      }
       if (i < T.m) {
         const TcBoxHost t = tb[T.rel];
         const BoxDesc& d = L.desc[T.b];
@@ -876,6 +941,8 @@ static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) 
   }
   return false;
 }
+constexpr int kGramChunk = 128;   // = TcSplit<TcGram>::steps
+
 static bool tc_kcontig(int which, bool side_b) {
   return side_b || which == kTcG1 || which == kTcGram;
 }
@@ -898,12 +965,13 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
         const int lp = l == 2 ? lpa : lpb;
         for (int x = 0; x < lp / 32; ++x)
           for (int y = 0; y < kg; ++y) units.push_back(TcUnit{e, l - 2, x, y});
-      } else {                           // product tiles
+      } else {                           // product tiles (and k chunks of the Gram matrix)
         const int tms = lpa / tc::kRows, tns = lpb / tc::kCols;
+        const int nchunk = which == kTcGram ? ((k + 15) / 16 + kGramChunk - 1) / kGramChunk : 1;
         for (int t = 0; t < tms * tns; ++t) {
           const int i0 = (t % tms) * tc::kRows, j0 = (t / tms) * tc::kCols;
           if (which == kTcGram && j0 + tc::kCols - 1 < i0) continue;
-          units.push_back(TcUnit{e, 0, t, 0});
+          for (int c = 0; c < nchunk; ++c) units.push_back(TcUnit{e, 0, t, c});
         }
       }
     }
@@ -946,8 +1014,9 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, const TcBoxHo
 
 void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
                        int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
-                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st) {
-  const TcExtra x{d_gb, gbuf};
+                       const TcUnit* d_units, const TcPlan& pl, cudaStream_t st,
+                       unsigned long long* gx, const int64_t* gx_off) {
+  const TcExtra x{d_gb, gbuf, gx, gx_off};
   switch (which) {
     case kTcG1: launch_tc<TcG1, 7, 6>("gemm_g1_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcG3: launch_tc<TcG3, 7, 6>("gemm_g3_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
@@ -963,6 +1032,19 @@ void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_
       else launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
       break;
   }
+}
+
+void launch_gram_finalize(const LevelDev& L, int b0, const TcUnit* d_boxes, int nboxes, int amax,
+                          const TcBoxHost* d_tb, const int* expo, const GramBoxHost* d_gb,
+                          double2* gbuf, unsigned long long* gx, const int64_t* gx_off, bool fp32,
+                          cudaStream_t st) {
+  if (nboxes <= 0) return;
+  const TcExtra x{d_gb, gbuf, gx, gx_off};
+  dim3 grid((unsigned)(((int64_t)amax * amax + 255) / 256), (unsigned)nboxes);
+  if (fp32)
+    FMMLU_LAUNCH("gram", st, (k_gram_finalize<4><<<grid, 256, 0, st>>>(L, b0, d_boxes, d_tb, expo, x)));
+  else
+    FMMLU_LAUNCH("gram", st, (k_gram_finalize<6><<<grid, 256, 0, st>>>(L, b0, d_boxes, d_tb, expo, x)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1025,9 +1107,11 @@ cudaError_t launch_root_factor_tc(double2* A, int n0, int nb, double2* W, int* s
     L.root_i0 = sp.i0;
     L.root_r = sp.r;
     launch_tc_planned(kTcRootW, L, 0, reinterpret_cast<const TcBoxHost*>(d_tb), d_slices,
-                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.pw, st);
+                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.pw, st,
+                      nullptr, nullptr);
     launch_tc_planned(kTcRootS, L, 0, reinterpret_cast<const TcBoxHost*>(d_tb), d_slices,
-                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.ps, st);
+                      reinterpret_cast<int*>(d_expo), nullptr, nullptr, false, du, sp.ps, st,
+                      nullptr, nullptr);
   }
   ck(cudaGetLastError());
   ck(cudaStreamSynchronize(st));   // the buffers above are freed next
