@@ -114,6 +114,29 @@ typedef struct fmmlu_opts {
                                  inverted again in fp64. Default 1e-9; 0
                                  inverts every such box again; < 0 turns the
                                  refinement off (fp64 Gauss-Jordan).        */
+  int solve_chunk;            /* rows of X_CR (forward sweep) and columns of
+                                 X_RC (backward sweep) per CTA in the solves:
+                                 0 (default) = chosen by the tuner when
+                                 autotune = 1, else 64; otherwise a multiple
+                                 of 16 in [16, 4096]. Results differ only in
+                                 the order of partial sums.                 */
+  int solve_graph;            /* 0: every solve launches its kernels;
+                                 1 (default): the second and later solves
+                                 with the same (nrhs, direction, stream)
+                                 replay the sweeps as one CUDA graph;
+                                 2: capture on the first solve. Solves with
+                                 opts.profile = 1 never use graphs.        */
+  int autotune;               /* 1 (default): on the first solve with a given
+                                 nrhs and direction, time the candidate
+                                 solve chunks (32, 64, 128, 256) on the
+                                 caller's right-hand sides and keep the
+                                 fastest; results are shared by all handles
+                                 with the same structure in the process.
+                                 0: use solve_chunk (or 64).               */
+  const char* autotune_cache; /* NULL or a file path: tuning results are read
+                                 from it (lines "key value") and appended to
+                                 it, so later processes skip the timing.
+                                 The string is copied by fmmlu_factor.     */
 } fmmlu_opts;
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if
@@ -155,6 +178,14 @@ int fmmlu_factor(const fmmlu_tree* tree, const double* points,
  *   b, x : device, complex128, N x nrhs column-major (ld = N), caller order.
  *          b and x may be the same array. b is not modified otherwise.
  *   nrhs : >= 1
+ * The call enqueues the work on `stream` and returns (with opts.profile = 1
+ * it waits for it); order later reads of x on other streams after it.
+ * Work vectors: the handle keeps those of the last four (nrhs, direction,
+ * stream) combinations, about 16 nrhs (N + 2 n0) bytes plus partial sums
+ * each, and their CUDA graphs (opts.solve_graph) until fmmlu_free. The first
+ * solve with a new nrhs and direction may time the candidate chunk sizes
+ * first (opts.autotune). Calls on one handle from several threads are
+ * serialised on the host.
  * Errors: INVALID_ARG, OOM, CUDA. */
 int fmmlu_solve(const fmmlu_handle* h, const double* b, double* x, int nrhs,
                 void* stream);

@@ -46,6 +46,10 @@ class fmmlu_opts(ctypes.Structure):
         ("schur_emulation", ctypes.c_int),
         ("id_method", ctypes.c_int),
         ("xrr_refine_tol", ctypes.c_double),
+        ("solve_chunk", ctypes.c_int),
+        ("solve_graph", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("autotune_cache", ctypes.c_char_p),
     ]
 
 
@@ -137,6 +141,8 @@ def fmmlu_default_opts(**overrides) -> fmmlu_opts:
             continue
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "autotune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 

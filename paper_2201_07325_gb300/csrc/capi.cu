@@ -16,10 +16,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <functional>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <set>
 #include <sstream>
 #include <stdexcept>
 #include <string>
@@ -159,6 +162,10 @@ void default_opts(fmmlu_opts* o) {
   o->schur_emulation = 1;
   o->id_method = FMMLU_ID_AUTO;
   o->xrr_refine_tol = 1e-9;
+  o->solve_chunk = 0;
+  o->solve_graph = 1;
+  o->autotune = 1;
+  o->autotune_cache = nullptr;
 }
 
 fmmlu_opts checked_opts(const fmmlu_opts* in) {
@@ -174,6 +181,10 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (o.id_method < 0 || o.id_method > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad id_method");
   if (o.schur_emulation < 0 || o.schur_emulation > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad schur_emulation");
   if (std::isnan(o.xrr_refine_tol)) throw Error(FMMLU_ERR_INVALID_ARG, "xrr_refine_tol is NaN");
+  if (o.solve_chunk != 0 && (o.solve_chunk < 16 || o.solve_chunk > 4096 || o.solve_chunk % 16))
+    throw Error(FMMLU_ERR_INVALID_ARG, "solve_chunk must be 0 or a multiple of 16 in [16, 4096]");
+  if (o.solve_graph < 0 || o.solve_graph > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad solve_graph");
+  if (o.autotune < 0 || o.autotune > 1) throw Error(FMMLU_ERR_INVALID_ARG, "bad autotune");
   return o;
 }
 
@@ -187,6 +198,46 @@ struct fmmlu_tree {
   ~fmmlu_tree() { if (d_perm) cudaFree(d_perm); }
 };
 
+namespace {
+
+// The chunk items of the solve sweeps for one chunk size (rows of C per CTA
+// in the forward sweep, columns in the backward one), on the device.
+struct SolvePlan {
+  int chunk = 0;
+  DevPool mem;
+  SolveBox* d_boxes = nullptr;
+  SweepItem* d_items = nullptr;
+  std::vector<SweepSeg> segs;   // elimination order
+  int64_t part_max = 1;         // partial sums per right-hand side (backward sweep)
+};
+
+// Work vectors of the solves with one (nrhs, direction, stream, chunk) and,
+// once that key has been used before (or always, by option), the sweeps
+// captured as one CUDA graph that later solves replay.
+struct SolveCtx {
+  int nrhs = 0;
+  bool adjoint = false;
+  cudaStream_t stream = nullptr;
+  std::shared_ptr<SolvePlan> plan;
+  DevPool mem;
+  double2 *v = nullptr, *part = nullptr, *vr = nullptr, *z = nullptr;
+  void* rscr = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  int64_t uses = 0;
+  uint64_t last = 0;
+  cudaEvent_t done = nullptr;   // recorded after each use on `stream`
+  ~SolveCtx() {
+    if (done) {
+      cudaEventSynchronize(done);
+      cudaEventDestroy(done);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+}  // namespace
+
 struct fmmlu_handle {
   uint32_t magic = kHandleMagic;
   int64_t n = 0;
@@ -195,10 +246,12 @@ struct fmmlu_handle {
   bool gram = false;           // ID by pivoted Cholesky of M^H M
   DevPool mem;                 // factors, plans, permutation
   int* d_perm = nullptr;
-  SolveBox* d_boxes = nullptr;
-  SweepItem* d_items = nullptr;
-  std::vector<SweepSeg> segs;  // elimination order
-  int64_t part_max = 0;        // partial sums per right-hand side (backward sweep)
+  std::vector<SolveBox> sboxes;   // eliminated boxes in elimination order (host)
+  std::vector<SweepSeg> sseg;     // their colour segments (items not yet built)
+  int chunk0 = kSweepChunkDefault;
+  int solve_graph = 1, autotune = 0;
+  std::string tune_cache;
+  uint64_t shape_key = 0;         // hash of the solve structure (tuning cache key)
   int n0 = 0, nb_root = 64;
   int* d_root_dofs = nullptr;
   double2* d_root = nullptr;
@@ -207,6 +260,16 @@ struct fmmlu_handle {
   int64_t arena_bytes = 0;
   bool profile = false;
   mutable Profiler prof;       // per-kernel accounting (factor + solves)
+  mutable std::mutex smu;      // guards the solve state below
+  mutable std::map<int, std::shared_ptr<SolvePlan>> plans;   // by chunk
+  mutable std::map<std::pair<int, int>, int> chunk_for;      // (nrhs, adjoint) -> chunk
+  mutable std::vector<std::unique_ptr<SolveCtx>> ctxs;
+  mutable cudaStream_t cap_stream = nullptr;
+  mutable uint64_t tick = 0;
+  ~fmmlu_handle() {
+    ctxs.clear();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace {
@@ -357,6 +420,51 @@ int status_to_code(int s, std::string& msg) {
   return 0;
 }
 
+// Chunk items of the solve sweeps for one chunk size: per box, C = [S | N]
+// in chunks of `chunk` rows (each chunk owns r partial sums, which the first
+// chunk also uses as the box's z scratch), and R and S in chunks of
+// kRowChunkHost rows.
+std::shared_ptr<SolvePlan> make_solve_plan(const fmmlu_handle* H, int chunk, cudaStream_t st) {
+  auto P = std::make_shared<SolvePlan>();
+  P->chunk = chunk;
+  std::vector<SolveBox> boxes = H->sboxes;
+  std::vector<SweepItem> items;
+  P->segs = H->sseg;
+  for (SweepSeg& sg : P->segs) {
+    int64_t part = 0;
+    sg.chunk = chunk;
+    sg.i0 = (int)items.size();
+    for (int q = sg.b0; q < sg.b0 + sg.nb; ++q) {
+      SolveBox& sb = boxes[q];
+      sb.zoff = (int)part;
+      sb.item_beg = (int)items.size();
+      const int c = sb.s + sb.n;
+      for (int c0 = 0; c0 == 0 || c0 < c; c0 += chunk) {
+        items.push_back(SweepItem{q, c0, std::min(c, c0 + chunk), (int)part});
+        part += sb.r;
+      }
+      sb.item_cnt = (int)items.size() - sb.item_beg;
+    }
+    sg.ni = (int)items.size() - sg.i0;
+    sg.ri0 = (int)items.size();
+    for (int q = sg.b0; q < sg.b0 + sg.nb; ++q)
+      for (int k0 = 0; k0 < boxes[q].r; k0 += kRowChunkHost)
+        items.push_back(SweepItem{q, k0, std::min(boxes[q].r, k0 + kRowChunkHost), 0});
+    sg.nri = (int)items.size() - sg.ri0;
+    sg.si0 = (int)items.size();
+    for (int q = sg.b0; q < sg.b0 + sg.nb; ++q)
+      for (int i0 = 0; i0 < boxes[q].s; i0 += kRowChunkHost)
+        items.push_back(SweepItem{q, i0, std::min(boxes[q].s, i0 + kRowChunkHost), 0});
+    sg.nsi = (int)items.size() - sg.si0;
+    sg.part = part;
+    P->part_max = std::max(P->part_max, part);
+  }
+  if (items.size() > (size_t)INT32_MAX) throw Error(FMMLU_ERR_LIMIT, "too many solve items");
+  P->d_boxes = P->mem.up(boxes, st);
+  P->d_items = P->mem.up(items, st);
+  return P;
+}
+
 void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, const double* w,
                  double k, double eps, const fmmlu_opts& opt, cudaStream_t st, fmmlu_handle* H) {
   const TreeHost& T = tree->T;
@@ -374,6 +482,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                         (opt.id_method == FMMLU_ID_AUTO && eps_id >= 1e-7);
   H->gram = use_gram;
   H->profile = opt.profile != 0;
+  H->chunk0 = opt.solve_chunk > 0 ? opt.solve_chunk : kSweepChunkDefault;
+  H->solve_graph = opt.solve_graph;
+  H->autotune = opt.solve_chunk == 0 ? opt.autotune : 0;
+  H->tune_cache = opt.autotune_cache ? opt.autotune_cache : "";
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
   Timer total_timer;
   DevPool work;   // freed at the end of the factorization
@@ -392,8 +504,6 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   js << "{\"n\": " << n << ", \"k\": " << k << ", \"eta\": " << H->eta << ", \"eps\": " << eps
      << ", \"precision\": \"" << (H->fp32 ? "mixed" : "fp64") << "\", \"id_method\": \"" << (H->gram ? "gram" : "householder") << "\", \"nlevels\": " << T.nlevels
      << ", \"levels\": [";
-  std::vector<SolveBox> plan;
-  std::vector<SweepItem> items;
   std::unique_ptr<LevelState> prev;
   int root_level = 1;
   bool first_level = true;
@@ -978,13 +1088,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         if (tc_r) H->prof.add_work(split_name, 0, split(s_ + n_, r_, r_) + split(s_ + n_, s_ + n_, r_));
       }
     }
-    // solve plan for this level
+    // solve plan for this level: the eliminated boxes of each colour in
+    // elimination order (their chunk items are built per chunk size by
+    // make_solve_plan)
     int64_t sum_a = 0, sum_s = 0, max_a = 0, max_r = 0;
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
-      int b0p = (int)plan.size();
-      int i0p = (int)items.size();
+      const int b0p = (int)H->sboxes.size();
       int rmax = 0, smax = 0;
-      int64_t part = 0;
       double fc = 0, bc = 0, fb = 0, bb = 0, seg_vbytes = 0;
       for (int e = seg_start[sgi]; e < seg_start[sgi + 1]; ++e) {
         const BoxDesc& d = desc[e];
@@ -994,23 +1104,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         max_r = std::max<int64_t>(max_r, rr.r);
         if (rr.r == 0) continue;
         int64_t ld3 = d.a + d.nmax;
-        SolveBox sb;
-        sb.r = rr.r; sb.s = rr.s; sb.n = rr.n; sb.zoff = (int)part;
+        SolveBox sb{};
+        sb.r = rr.r; sb.s = rr.s; sb.n = rr.n;
         sb.idx = d_iarena + d.idx_off;
         sb.T = d_arena + d.T_off; sb.ldT = d.a;
         sb.Xinv = d_arena + d.Xinv_off; sb.ldX = d.a;
         sb.XCR = d_arena + d.G3_off + (int64_t)rr.s * ld3; sb.ldL = (int)ld3;
         sb.XRC = d_arena + d.G1_off + rr.s; sb.ldU = d.a;
-        sb.item_beg = (int)items.size();
-        // at least one C chunk per box: its partial slots double as the
-        // box's z scratch, and it stores b_R = z in the forward sweep
-        for (int c0 = 0; c0 == 0 || c0 < rr.s + rr.n; c0 += kSweepChunk) {
-          items.push_back(SweepItem{(int)plan.size(), c0, std::min(rr.s + rr.n, c0 + kSweepChunk),
-                                    (int)part});
-          part += rr.r;
-        }
-        sb.item_cnt = (int)items.size() - sb.item_beg;
-        plan.push_back(sb);
+        H->sboxes.push_back(sb);
         rmax = std::max(rmax, rr.r);
         smax = std::max(smax, rr.s);
         double ec = (double)(rr.s + rr.n) * rr.r;
@@ -1021,27 +1122,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         H->factor_entries += (int64_t)rr.s * rr.r + (int64_t)rr.r * rr.r +
                              2 * (int64_t)(rr.s + rr.n) * rr.r;
       }
-      int cnt = (int)plan.size() - b0p;
+      const int cnt = (int)H->sboxes.size() - b0p;
       if (cnt > 0) {
-        SweepSeg sg;
+        SweepSeg sg{};
         sg.b0 = b0p; sg.nb = cnt;
-        sg.i0 = i0p; sg.ni = (int)items.size() - i0p;
-        // row chunks of the R and S products
-        sg.ri0 = (int)items.size();
-        for (int q = b0p; q < b0p + cnt; ++q)
-          for (int k0 = 0; k0 < plan[q].r; k0 += kRowChunkHost)
-            items.push_back(SweepItem{q, k0, std::min(plan[q].r, k0 + kRowChunkHost), 0});
-        sg.nri = (int)items.size() - sg.ri0;
-        sg.si0 = (int)items.size();
-        for (int q = b0p; q < b0p + cnt; ++q)
-          for (int i0s = 0; i0s < plan[q].s; i0s += kRowChunkHost)
-            items.push_back(SweepItem{q, i0s, std::min(plan[q].s, i0s + kRowChunkHost), 0});
-        sg.nsi = (int)items.size() - sg.si0;
-        sg.rmax = rmax; sg.smax = smax; sg.part = part;
+        sg.rmax = rmax; sg.smax = smax;
         sg.flops_c = fc; sg.bytes_c = bc; sg.flops_b = fb; sg.bytes_b = bb;
         sg.bytes_per_rhs = seg_vbytes;
-        H->segs.push_back(sg);
-        H->part_max = std::max(H->part_max, part);
+        H->sseg.push_back(sg);
       }
     }
     double lms = lt.ms();
@@ -1126,8 +1214,18 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     H->factor_entries += (int64_t)n0 * n0;
   }
   double root_ms = rt.ms();
-  H->d_boxes = H->mem.up(plan, st);
-  H->d_items = H->mem.up(items, st);
+  H->plans[H->chunk0] = make_solve_plan(H, H->chunk0, st);
+  {
+    // FNV-1a over the solve's structure: the key of tuned solve settings
+    uint64_t hs = 1469598103934665603ull;
+    auto mix = [&](int64_t v) {
+      for (int i = 0; i < 8; ++i) { hs ^= (uint64_t)(v >> (8 * i)) & 0xffu; hs *= 1099511628211ull; }
+    };
+    mix(n); mix(n0);
+    for (const SolveBox& sb : H->sboxes) { mix(sb.r); mix(sb.s); mix(sb.n); }
+    for (const SweepSeg& sg : H->sseg) { mix(sg.b0); mix(sg.nb); }
+    H->shape_key = hs;
+  }
   CK(cudaStreamSynchronize(st));
   double tot_ms = total_timer.ms();
   if (opt.verbose)
@@ -1135,52 +1233,252 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                  root_level, n0, root_ms, tot_ms, H->factor_entries * 16.0 / 1e6);
   js << "], \"root_level\": " << root_level << ", \"n0\": " << n0 << ", \"root_ms\": " << root_ms
      << ", \"factor_ms\": " << tot_ms << ", \"factor_bytes\": " << H->factor_entries * 16
-     << ", \"arena_bytes\": " << H->arena_bytes << ", \"eliminated_boxes\": " << plan.size()
-     << ", \"colour_segments\": " << H->segs.size() << "}";
+     << ", \"arena_bytes\": " << H->arena_bytes << ", \"eliminated_boxes\": " << H->sboxes.size()
+     << ", \"colour_segments\": " << H->sseg.size() << "}";
   H->stats = js.str();
+}
+
+// ---------------------------------------------------------------------------
+// solve runtime: plans per chunk size, work vectors per (nrhs, direction,
+// stream, chunk), CUDA graphs of the sweeps, and the chunk-size tuner
+// ---------------------------------------------------------------------------
+
+constexpr size_t kMaxSolveCtx = 4;
+constexpr int kTuneChunks[] = {32, 64, 128, 256};
+
+std::shared_ptr<SolvePlan> get_plan(const fmmlu_handle* H, int chunk, cudaStream_t st) {
+  auto it = H->plans.find(chunk);
+  if (it != H->plans.end()) return it->second;
+  auto P = make_solve_plan(H, chunk, st);
+  H->plans[chunk] = P;
+  return P;
+}
+
+void alloc_ctx(const fmmlu_handle* H, SolveCtx& c) {
+  const int64_t n = H->n;
+  c.v = c.mem.get<double2>((size_t)n * c.nrhs);
+  c.part = c.mem.get<double2>((size_t)c.plan->part_max * c.nrhs);
+  if (H->n0 > 0) {
+    c.vr = c.mem.get<double2>((size_t)H->n0 * c.nrhs);
+    c.z = c.mem.get<double2>((size_t)H->n0 * c.nrhs);
+    c.rscr = c.mem.get<unsigned char>(root_solve_scratch_bytes(H->n0, H->nb_root, c.nrhs));
+  }
+}
+
+// forward sweep, root, backward sweep on the permuted vectors c.v (in place)
+void run_sweeps(const fmmlu_handle* H, const SolveCtx& c, cudaStream_t st) {
+  const SolvePlan& P = *c.plan;
+  const int64_t n = H->n, pst = P.part_max;
+  for (const auto& sg : P.segs)
+    launch_sweep(P.d_boxes, P.d_items, sg, c.v, n, c.nrhs, false, c.adjoint, c.part, pst, st);
+  if (H->n0 > 0) {
+    launch_root_gather(c.v, H->d_root_dofs, H->n0, n, c.nrhs, c.vr, st);
+    CK(launch_root_solve(H->d_root, H->n0, H->nb_root, c.vr, c.z, c.rscr, c.nrhs, c.adjoint, st));
+    launch_root_scatter(c.vr, H->d_root_dofs, H->n0, n, c.nrhs, c.v, st);
+  }
+  for (auto it = P.segs.rbegin(); it != P.segs.rend(); ++it)
+    launch_sweep(P.d_boxes, P.d_items, *it, c.v, n, c.nrhs, true, c.adjoint, c.part, pst, st);
+}
+
+// Record the sweeps of c into a CUDA graph on the handle's own capture stream
+// (the caller's stream may be the legacy default stream, which cannot be
+// captured); the graph is launched on the caller's stream.
+void capture_ctx(const fmmlu_handle* H, SolveCtx& c) {
+  if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+  prepare_solve_kernels();
+  ProfScope none(nullptr);
+  const int64_t l0 = launches_total();
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    run_sweeps(H, c, H->cap_stream);
+  } catch (...) {
+    cudaStreamEndCapture(H->cap_stream, &g);
+    if (g) cudaGraphDestroy(g);
+    launches_add(l0 - launches_total());
+    throw;
+  }
+  CK(cudaStreamEndCapture(H->cap_stream, &g));
+  c.graph_kernels = launches_total() - l0;
+  launches_add(-c.graph_kernels);
+  cudaError_t e = cudaGraphInstantiate(&c.exec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+}
+
+SolveCtx* get_ctx(const fmmlu_handle* H, int nrhs, bool adjoint, cudaStream_t st, int chunk) {
+  for (auto& c : H->ctxs)
+    if (c->nrhs == nrhs && c->adjoint == adjoint && c->stream == st && c->plan->chunk == chunk)
+      return c.get();
+  if (H->ctxs.size() >= kMaxSolveCtx) {   // drop the least recently used (waits for it)
+    auto lru = std::min_element(H->ctxs.begin(), H->ctxs.end(),
+                                [](const std::unique_ptr<SolveCtx>& a,
+                                   const std::unique_ptr<SolveCtx>& b) { return a->last < b->last; });
+    H->ctxs.erase(lru);
+  }
+  auto c = std::make_unique<SolveCtx>();
+  c->nrhs = nrhs;
+  c->adjoint = adjoint;
+  c->stream = st;
+  c->plan = get_plan(H, chunk, st);
+  alloc_ctx(H, *c);
+  CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+  H->ctxs.push_back(std::move(c));
+  return H->ctxs.back().get();
+}
+
+// process-wide tuning results (key -> chunk), optionally kept in text files
+// of "key value" lines: a file is read on first use and every result this
+// process uses that the file lacks is appended to it
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+std::map<std::string, std::set<std::string>> g_tune_files;
+
+bool valid_chunk(int c) { return c >= 16 && c <= 4096 && c % 16 == 0; }
+
+std::set<std::string>& tune_file_keys(const std::string& path) {
+  auto it = g_tune_files.find(path);
+  if (it != g_tune_files.end()) return it->second;
+  std::set<std::string>& keys = g_tune_files[path];
+  std::ifstream f(path);
+  std::string k;
+  long v;
+  while (f >> k >> v)
+    if (valid_chunk((int)v)) {
+      g_tune[k] = (int)v;
+      keys.insert(k);
+    }
+  return keys;
+}
+
+bool tune_lookup(const std::string& path, const std::string& key, int* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (!path.empty()) tune_file_keys(path);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(const std::string& path, const std::string& key, int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = v;
+  if (path.empty()) return;
+  std::set<std::string>& keys = tune_file_keys(path);
+  if (keys.count(key)) return;
+  std::ofstream f(path, std::ios::app);
+  if (f) {
+    f << key << ' ' << v << '\n';
+    keys.insert(key);
+  }
+}
+
+std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
+    return "unknown";
+  std::string s = pr.name;
+  for (char& ch : s)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return s + "_sm" + std::to_string(pr.major) + std::to_string(pr.minor);
+}
+
+// Time the whole solve (both sweeps and the root) once per candidate chunk on
+// the caller's right-hand sides; the fastest of three timed runs after one
+// warm-up counts. Every candidate computes the same solution (only the order
+// of the partial sums differs).
+int tune_solve_chunk(const fmmlu_handle* H, int nrhs, bool adjoint, const double* b,
+                     cudaStream_t st) {
+  ProfScope none(nullptr);
+  struct Ev {
+    cudaEvent_t e = nullptr;
+    ~Ev() { if (e) cudaEventDestroy(e); }
+  } e0, e1;
+  CK(cudaEventCreate(&e0.e));
+  CK(cudaEventCreate(&e1.e));
+  float best = INFINITY;
+  int bestc = H->chunk0;
+  for (int chunk : kTuneChunks) {
+    SolveCtx t;
+    t.nrhs = nrhs;
+    t.adjoint = adjoint;
+    t.plan = get_plan(H, chunk, st);
+    alloc_ctx(H, t);
+    float tmin = INFINITY;
+    for (int rep = 0; rep < 4; ++rep) {
+      launch_gather_vec(reinterpret_cast<const double2*>(b), H->d_perm, H->n, nrhs, t.v, st);
+      CK(cudaEventRecord(e0.e, st));
+      run_sweeps(H, t, st);
+      CK(cudaEventRecord(e1.e, st));
+      CK(cudaEventSynchronize(e1.e));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    if (tmin < best) {
+      best = tmin;
+      bestc = chunk;
+    }
+  }
+  return bestc;
+}
+
+int choose_chunk(const fmmlu_handle* H, int nrhs, bool adjoint, const double* b, cudaStream_t st) {
+  const auto key = std::make_pair(nrhs, adjoint ? 1 : 0);
+  auto it = H->chunk_for.find(key);
+  if (it != H->chunk_for.end()) return it->second;
+  int chunk = H->chunk0;
+  if (H->autotune) {
+    char hx[32];
+    std::snprintf(hx, sizeof(hx), "%016llx", (unsigned long long)H->shape_key);
+    const std::string tk = "solve_chunk|" + device_tag() + "|" + hx + "|nrhs=" +
+                           std::to_string(nrhs) + "|adj=" + (adjoint ? "1" : "0");
+    if (!tune_lookup(H->tune_cache, tk, &chunk)) chunk = tune_solve_chunk(H, nrhs, adjoint, b, st);
+    tune_store(H->tune_cache, tk, chunk);
+  }
+  H->chunk_for[key] = chunk;
+  return chunk;
 }
 
 void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, bool adjoint,
                 cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(H->smu);
+  const int chunk = choose_chunk(H, nrhs, adjoint, b, st);
+  SolveCtx* c = get_ctx(H, nrhs, adjoint, st, chunk);
+  const bool graph =
+      !H->profile && (H->solve_graph == 2 || (H->solve_graph == 1 && c->uses >= 1));
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
-  int64_t n = H->n;
-  DevPool w;
-  double2* v = w.get<double2>((size_t)n * nrhs);
-  const int64_t pst = std::max<int64_t>(1, H->part_max);
-  double2* part = w.get<double2>((size_t)pst * nrhs);
-  launch_gather_vec(reinterpret_cast<const double2*>(b), H->d_perm, n, nrhs, v, st);
-  for (const auto& sg : H->segs)
-    launch_sweep(H->d_boxes, H->d_items, sg, v, n, nrhs, false, adjoint, part, pst, st);
-  if (H->n0 > 0) {
-    int n0 = H->n0;
-    double2* vr = w.get<double2>((size_t)n0 * nrhs);
-    double2* z = w.get<double2>((size_t)n0 * nrhs);
-    int nblk = std::max(1, (n0 + 511) / 512);
-    double2* partial = w.get<double2>((size_t)nrhs * nblk * 256);
-    launch_root_gather(v, H->d_root_dofs, n0, n, nrhs, vr, st);
-    launch_root_solve(H->d_root, n0, H->nb_root, vr, z, partial, nrhs, adjoint, st);
-    launch_root_scatter(vr, H->d_root_dofs, n0, n, nrhs, v, st);
+  const int64_t n = H->n;
+  launch_gather_vec(reinterpret_cast<const double2*>(b), H->d_perm, n, nrhs, c->v, st);
+  if (graph) {
+    if (!c->exec) capture_ctx(H, *c);
+    CK(cudaGraphLaunch(c->exec, st));
+    launches_add(c->graph_kernels);
+  } else {
+    run_sweeps(H, *c, st);
   }
-  for (auto it = H->segs.rbegin(); it != H->segs.rend(); ++it)
-    launch_sweep(H->d_boxes, H->d_items, *it, v, n, nrhs, true, adjoint, part, pst, st);
-  launch_scatter_vec(v, H->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
+  launch_scatter_vec(c->v, H->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(st));   // the work buffers are freed on return
+  CK(cudaEventRecord(c->done, st));
+  ++c->uses;
+  c->last = ++H->tick;
   if (H->profile) {
+    CK(cudaStreamSynchronize(st));
     H->prof.resolve();
-    for (const auto& sg : H->segs) {
+    for (const auto& sg : c->plan->segs) {
       H->prof.add_work("sweep_fwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
       H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
       H->prof.add_work("sweep_bwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
       H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
     }
-    int n0 = H->n0;
+    const int n0 = H->n0;
     for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
-      double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
+      const double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
       H->prof.add_work("root_fwd", 8.0 * nrhs * (r_ * r_ + later * r_),
                        16.0 * (r_ * r_ + later * r_ + 2.0 * nrhs * (later + r_)));
-      H->prof.add_work(later > 0 ? "root_bwd1" : "root_bwd2", 8.0 * nrhs * later * r_,
-                       16.0 * (later * r_ + nrhs * later));
+      H->prof.add_work("root_bwd", 8.0 * nrhs * (later * r_ + r_ * r_),
+                       16.0 * (later * r_ + r_ * r_ + nrhs * (later + 2.0 * r_)));
     }
   }
 }
@@ -1435,14 +1733,24 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
     if (!h || h->magic != kHandleMagic || !b || !x || nrhs < 1)
       throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
     cudaStream_t st = (cudaStream_t)stream;
+    const bool adj = adjoint != 0;
+    std::shared_ptr<SolvePlan> plan;
+    {
+      // the plan of an earlier solve with this nrhs and direction, else the
+      // factorization's own (both exist already: nothing is built here)
+      std::lock_guard<std::mutex> lock(h->smu);
+      int chunk = h->chunk0;
+      auto it = h->chunk_for.find(std::make_pair(nrhs, adj ? 1 : 0));
+      if (it != h->chunk_for.end()) chunk = it->second;
+      auto pit = h->plans.find(chunk);
+      plan = pit != h->plans.end() ? pit->second : h->plans.at(h->chunk0);
+    }
     const int64_t n = h->n;
     const int n0 = h->n0;
-    const int nblk = std::max(1, (n0 + 511) / 512);
     const size_t bv = round256((size_t)16 * n * nrhs);
     const size_t br = round256((size_t)16 * n0 * nrhs);
-    const size_t bp = round256((size_t)16 * nrhs * nblk * 256);
-    const int64_t pst = std::max<int64_t>(1, h->part_max);
-    const size_t bs = round256((size_t)16 * nrhs * pst);
+    const size_t bp = round256(root_solve_scratch_bytes(n0, h->nb_root, nrhs));
+    const size_t bs = round256((size_t)16 * nrhs * plan->part_max);
     const size_t need = bv + 2 * br + bp + bs;
     if (need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
       throw Error(FMMLU_ERR_LIMIT,
@@ -1450,23 +1758,18 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
                       " bytes of work space; the fixed array holds " +
                       std::to_string((size_t)FMMLU_NOALLOC_SCRATCH_BYTES));
     unsigned char* base = noalloc_scratch_for_current_device();
-    double2* v = reinterpret_cast<double2*>(base);
-    double2* vr = reinterpret_cast<double2*>(base + bv);
-    double2* z = reinterpret_cast<double2*>(base + bv + br);
-    double2* partial = reinterpret_cast<double2*>(base + bv + 2 * br);
-    double2* spart = reinterpret_cast<double2*>(base + bv + 2 * br + bp);
-    const bool adj = adjoint != 0;
-    launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, v, st);
-    for (const auto& sg : h->segs)
-      launch_sweep(h->d_boxes, h->d_items, sg, v, n, nrhs, false, adj, spart, pst, st);
-    if (n0 > 0) {
-      launch_root_gather(v, h->d_root_dofs, n0, n, nrhs, vr, st);
-      launch_root_solve(h->d_root, n0, h->nb_root, vr, z, partial, nrhs, adj, st);
-      launch_root_scatter(vr, h->d_root_dofs, n0, n, nrhs, v, st);
-    }
-    for (auto it = h->segs.rbegin(); it != h->segs.rend(); ++it)
-      launch_sweep(h->d_boxes, h->d_items, *it, v, n, nrhs, true, adj, spart, pst, st);
-    launch_scatter_vec(v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
+    SolveCtx c;   // views into the fixed array; owns nothing
+    c.nrhs = nrhs;
+    c.adjoint = adj;
+    c.plan = plan;
+    c.v = reinterpret_cast<double2*>(base);
+    c.vr = reinterpret_cast<double2*>(base + bv);
+    c.z = reinterpret_cast<double2*>(base + bv + br);
+    c.rscr = base + bv + 2 * br;
+    c.part = reinterpret_cast<double2*>(base + bv + 2 * br + bp);
+    launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, c.v, st);
+    run_sweeps(h, c, st);
+    launch_scatter_vec(c.v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
     CK(cudaGetLastError());
   });
 }

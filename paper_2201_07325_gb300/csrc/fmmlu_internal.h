@@ -114,7 +114,7 @@ struct SolveBox {
 };
 
 // a chunk [c0, c1) of a box's C rows (forward) or columns (backward)
-constexpr int kSweepChunk = 256;
+constexpr int kSweepChunkDefault = 64;
 struct SweepItem {
   int box;       // index into the SolveBox array
   int c0, c1;
@@ -127,6 +127,7 @@ struct SweepSeg {
   int ri0, nri;  // R-row chunk items
   int si0, nsi;  // S-row chunk items
   int rmax, smax;
+  int chunk;     // rows (forward) or columns (backward) of C per item
   int64_t part;  // partial sums needed per right-hand side
   double flops_c, bytes_c;   // per sweep: X_CR / X_RC products (per rhs: flops)
   double flops_b, bytes_b;   // per sweep: T and X_RR^{-1} products
@@ -298,6 +299,8 @@ void launch_gather_vec(const double2* b, const int* perm, int64_t n, int nrhs,
                        double2* v, cudaStream_t st);
 void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs,
                         double2* x, cudaStream_t st);
+// one-time kernel attributes of the sweeps (call before a stream capture)
+void prepare_solve_kernels();
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
                   double2* partial, int64_t pstride, cudaStream_t st);
@@ -305,7 +308,9 @@ void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n,
                         int nrhs, double2* vr, cudaStream_t st);
 void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,
                          int nrhs, double2* v, cudaStream_t st);
-void launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
-                       double2* partial, int nrhs, bool adjoint, cudaStream_t st);
+// scratch: root_solve_scratch_bytes(n0, nb, nrhs) bytes of device memory
+size_t root_solve_scratch_bytes(int n0, int nb, int nrhs);
+cudaError_t launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
+                              void* scratch, int nrhs, bool adjoint, cudaStream_t st);
 
 }  // namespace fmmlu

@@ -12,6 +12,7 @@ thread_local Profiler* g_prof = nullptr;
 static std::atomic<int64_t> g_launches{0};
 
 int64_t launches_total() { return g_launches.load(); }
+void launches_add(int64_t d) { g_launches.fetch_add(d); }
 
 void launch_begin(const char* name, cudaStream_t st) {
   g_launches.fetch_add(1);

@@ -37,6 +37,9 @@ struct Profiler {
 
 extern thread_local Profiler* g_prof;
 int64_t launches_total();
+// adjusts the count: kernels recorded into a CUDA graph count when the graph
+// is launched, not when it is captured
+void launches_add(int64_t d);
 
 // sets g_prof for a scope
 struct ProfScope {

@@ -40,7 +40,7 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs, 
 
 // Box sweeps, three launches per colour and direction, every product split
 // into row chunks so that one large box uses many SMs (GB300's fp64 rate per
-// SM is ~4 GFLOP/s, so one CTA per box would be bound by a single SM):
+// SM is ~7 GFLOP/s, so one CTA per box would be bound by a single SM):
 //   forward:  k_sw_y  (R chunks)  b_R -= op(T)^T b_S
 //             k_sw_z  (R chunks)  z = op(X_RR^{-1}) b_R  (into the box's scratch)
 //             k_fwd_c (C chunks)  b_C -= op(X_CR) z; the first chunk stores b_R = z
@@ -49,51 +49,99 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs, 
 //             k_sw_xs (S chunks)  x_S -= op(T) x_R
 // op() is the identity for A^{-1}; for A^{-H} the roles are (X_RC^H, X_CR^H,
 // X_RR^{-H}, conj(T)).
+//
+// Every product is a matrix-vector product of a column-major block with a
+// vector staged in shared memory. At one right-hand side the block is read
+// once, 16 B per 8 flops, so a CTA must keep many loads in flight: each thread
+// issues four independent loads per step, and the threads are laid out so
+// that a warp reads consecutive addresses (lanes over the contiguous index).
 
-constexpr int kRowChunk = 16;   // output rows per CTA of the R and S products
+template <bool kCj>
+__device__ __forceinline__ void cf(double2& acc, double2 a, double2 b) {
+  if (kCj) cfma_cj(acc, a, b); else cfma(acc, a, b);
+}
 
-// out[k - k0] = sum_l op(M)(k, l) x[l] for k in [k0, k0 + kc), kc <= 16, with
-// 256 threads and x in shared memory. kRows: element (k, l) at M[k + l ld]
-// (a half-warp reads 16 consecutive k); else at M[l + k ld] (16 consecutive
-// l). cj conjugates the matrix element.
-template <bool kRows>
-__device__ __forceinline__ void chunk_mv(const double2* __restrict__ M, int64_t ld, bool cj,
-                                         const double2* x, int L, int k0, int kc, double2* red,
-                                         double2* out) {
+// store(o, y_o) with y_o = sum_{q < nq} op(M[o + q ld]) x[q], o < no: the
+// output index is the contiguous one. 256 threads: consecutive threads take
+// consecutive outputs (16 or 32 per tile); when fewer than 256 outputs are
+// left, the remaining threads split q into interleaved groups whose sums meet
+// in red (256 entries).
+template <bool kCj, class Store>
+__device__ __forceinline__ void mv_cols(const double2* __restrict__ M, int64_t ld,
+                                        const double2* x, int no, int nq, double2* red,
+                                        Store store) {
   const int t = threadIdx.x;
-  double2 acc = mk(0.0, 0.0);
-  if (kRows) {
-    const int row = t & 15, g = t >> 4;
-    if (row < kc) {
-      const double2* Mr = M + (k0 + row);
-      for (int l = g; l < L; l += 16) {
-        const double2 m = Mr[(int64_t)l * ld];
-        if (cj) cfma_cj(acc, m, x[l]); else cfma(acc, m, x[l]);
+  const int ot = no <= 16 ? 16 : 32;
+  int span = ot;
+  while (span < no && span < 256) span <<= 1;
+  const int qg = 256 / span;
+  const int oi = t % span, g = t / span;
+  for (int ob = 0; ob < no; ob += span) {
+    const int o = ob + oi;
+    double2 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+    if (o < no) {
+      const double2* Mo = M + o;
+      int q = g;
+      for (; q + 3 * qg < nq; q += 4 * qg) {
+        const double2 m0 = Mo[(int64_t)q * ld];
+        const double2 m1 = Mo[(int64_t)(q + qg) * ld];
+        const double2 m2 = Mo[(int64_t)(q + 2 * qg) * ld];
+        const double2 m3 = Mo[(int64_t)(q + 3 * qg) * ld];
+        cf<kCj>(a0, m0, x[q]);
+        cf<kCj>(a1, m1, x[q + qg]);
+        cf<kCj>(a0, m2, x[q + 2 * qg]);
+        cf<kCj>(a1, m3, x[q + 3 * qg]);
       }
+      for (; q < nq; q += qg) cf<kCj>(a0, Mo[(int64_t)q * ld], x[q]);
     }
-    red[t] = acc;
-    __syncthreads();
-    if (t < kRowChunk) {
-      double2 sum = mk(0.0, 0.0);
-      for (int q = 0; q < 16; ++q) sum = cadd(sum, red[q * 16 + t]);
-      out[t] = sum;
-    }
-  } else {
-    const int row = t >> 4, ln = t & 15;
-    if (row < kc) {
-      const double2* Mc = M + (int64_t)(k0 + row) * ld;
-      for (int l = ln; l < L; l += 16) {
-        const double2 m = Mc[l];
-        if (cj) cfma_cj(acc, m, x[l]); else cfma(acc, m, x[l]);
+    const double2 acc = cadd(a0, a1);
+    if (qg == 1) {
+      if (o < no) store(o, acc);
+    } else {
+      red[t] = acc;
+      __syncthreads();
+      if (g == 0 && o < no) {
+        double2 s = acc;
+        for (int gg = 1; gg < qg; ++gg) s = cadd(s, red[gg * span + oi]);
+        store(o, s);
       }
+      __syncthreads();
     }
-    for (int o = 8; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (ln == 0) out[row] = acc;
   }
-  __syncthreads();
+}
+
+// store(o, y_o) with y_o = sum_{q < nq} op(M[q + o ld]) x[q], o < no: every
+// output is a dot product along a contiguous column. A group of 8, 16 or 32
+// lanes (by nq) per output, shuffle reduction inside the group.
+template <bool kCj, class Store>
+__device__ __forceinline__ void mv_dots(const double2* __restrict__ M, int64_t ld,
+                                        const double2* x, int no, int nq, Store store) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sw = nq > 16 ? 32 : (nq > 8 ? 16 : 8);
+  const int per = 32 / sw;
+  const int sl = lane % sw, sub = lane / sw;
+  for (int ob = w * per; ob < no; ob += nw * per) {
+    const int o = ob + sub;
+    double2 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+    if (o < no) {
+      const double2* Mo = M + (int64_t)o * ld;
+      int q = sl;
+      for (; q + 3 * sw < nq; q += 4 * sw) {
+        const double2 m0 = Mo[q], m1 = Mo[q + sw], m2 = Mo[q + 2 * sw], m3 = Mo[q + 3 * sw];
+        cf<kCj>(a0, m0, x[q]);
+        cf<kCj>(a1, m1, x[q + sw]);
+        cf<kCj>(a0, m2, x[q + 2 * sw]);
+        cf<kCj>(a1, m3, x[q + 3 * sw]);
+      }
+      for (; q < nq; q += sw) cf<kCj>(a0, Mo[q], x[q]);
+    }
+    double2 acc = cadd(a0, a1);
+    for (int off = sw >> 1; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (sl == 0 && o < no) store(o, acc);
+  }
 }
 
 // forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
@@ -104,19 +152,24 @@ __global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   double2* vc = v + blockIdx.y * n;
-  double2* red = sh;            // 256
-  double2* out = sh + 256;      // 16
-  double2* bS = sh + 272;       // s
-  const int* Ridx = B.idx;
+  double2* bS = sh;
+  const int* Ridx = B.idx + it.c0;
   const int* Sidx = B.idx + B.r;
   for (int i = threadIdx.x; i < B.s; i += blockDim.x) bS[i] = vc[Sidx[i]];
   __syncthreads();
   const int kc = it.c1 - it.c0;
-  chunk_mv<false>(B.T, B.ldT, adjoint != 0, bS, B.s, it.c0, kc, red, out);
-  if (threadIdx.x < kc) {
-    const int dof = Ridx[it.c0 + threadIdx.x];
-    vc[dof] = csub(vc[dof], out[threadIdx.x]);
-  }
+  auto st = [=](int o, double2 y) { const int dof = Ridx[o]; vc[dof] = csub(vc[dof], y); };
+  const double2* M = B.T + (int64_t)it.c0 * B.ldT;
+  if (adjoint) mv_dots<true>(M, B.ldT, bS, kc, B.s, st);
+  else mv_dots<false>(M, B.ldT, bS, kc, B.s, st);
+}
+
+// z_k = op(X_RR^{-1})(k, :) y for the chunk's rows k; store(k - c0, z_k)
+template <class Store>
+__device__ __forceinline__ void xinv_rows(const SolveBox& B, int c0, int kc, const double2* y,
+                                          double2* red, bool adjoint, Store store) {
+  if (!adjoint) mv_cols<false>(B.Xinv + c0, B.ldX, y, kc, B.r, red, store);
+  else mv_dots<true>(B.Xinv + (int64_t)c0 * B.ldX, B.ldX, y, kc, B.r, store);
 }
 
 // forward: z = op(X_RR^{-1}) b_R for the chunk's rows, into the box's scratch
@@ -130,14 +183,12 @@ __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes
   const SolveBox B = boxes[it.box];
   const double2* vc = v + blockIdx.y * n;
   double2* red = sh;
-  double2* out = sh + 256;
-  double2* y = sh + 272;        // r
+  double2* y = sh + 256;        // r
   for (int k = threadIdx.x; k < B.r; k += blockDim.x) y[k] = vc[B.idx[k]];
   __syncthreads();
-  const int kc = it.c1 - it.c0;
-  if (!adjoint) chunk_mv<true>(B.Xinv, B.ldX, false, y, B.r, it.c0, kc, red, out);
-  else chunk_mv<false>(B.Xinv, B.ldX, true, y, B.r, it.c0, kc, red, out);
-  if (threadIdx.x < kc) zbuf[blockIdx.y * zstride + B.zoff + it.c0 + threadIdx.x] = out[threadIdx.x];
+  double2* zo = zbuf + blockIdx.y * zstride + B.zoff + it.c0;
+  xinv_rows(B, it.c0, it.c1 - it.c0, y, red, adjoint != 0,
+            [=](int o, double2 z) { zo[o] = z; });
 }
 
 // backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = sum of the partials
@@ -152,21 +203,18 @@ __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxe
   double2* vc = v + blockIdx.y * n;
   const double2* pc = partial + blockIdx.y * pstride;
   double2* red = sh;
-  double2* out = sh + 256;
-  double2* tt = sh + 272;       // r
+  double2* tt = sh + 256;       // r
   for (int k = threadIdx.x; k < B.r; k += blockDim.x) {
     double2 acc = mk(0.0, 0.0);
     for (int q = B.item_beg; q < B.item_beg + B.item_cnt; ++q) acc = cadd(acc, pc[items[q].part + k]);
     tt[k] = acc;
   }
   __syncthreads();
-  const int kc = it.c1 - it.c0;
-  if (!adjoint) chunk_mv<true>(B.Xinv, B.ldX, false, tt, B.r, it.c0, kc, red, out);
-  else chunk_mv<false>(B.Xinv, B.ldX, true, tt, B.r, it.c0, kc, red, out);
-  if (threadIdx.x < kc) {
-    const int dof = B.idx[it.c0 + threadIdx.x];
-    vc[dof] = csub(vc[dof], out[threadIdx.x]);
-  }
+  const int* Ridx = B.idx + it.c0;
+  xinv_rows(B, it.c0, it.c1 - it.c0, tt, red, adjoint != 0, [=](int o, double2 y) {
+    const int dof = Ridx[o];
+    vc[dof] = csub(vc[dof], y);
+  });
 }
 
 // backward: x_S[i] -= sum_k op(T)(i, k) x_R[k] for the chunk's rows i
@@ -178,46 +226,42 @@ __global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxe
   const SolveBox B = boxes[it.box];
   double2* vc = v + blockIdx.y * n;
   double2* red = sh;
-  double2* out = sh + 256;
-  double2* xr = sh + 272;       // r
+  double2* xr = sh + 256;       // r
   for (int k = threadIdx.x; k < B.r; k += blockDim.x) xr[k] = vc[B.idx[k]];
   __syncthreads();
-  const int kc = it.c1 - it.c0;
-  chunk_mv<true>(B.T, B.ldT, adjoint != 0, xr, B.r, it.c0, kc, red, out);
-  if (threadIdx.x < kc) {
-    const int dof = B.idx[B.r + it.c0 + threadIdx.x];
-    vc[dof] = csub(vc[dof], out[threadIdx.x]);
-  }
+  const int* Sidx = B.idx + B.r + it.c0;
+  auto st = [=](int o, double2 y) { const int dof = Sidx[o]; vc[dof] = csub(vc[dof], y); };
+  if (adjoint) mv_cols<true>(B.T + it.c0, B.ldT, xr, it.c1 - it.c0, B.r, red, st);
+  else mv_cols<false>(B.T + it.c0, B.ldT, xr, it.c1 - it.c0, B.r, red, st);
 }
 
+// forward: b_C -= op(X_CR) z on the chunk's rows of C
 __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
                                                const double2* __restrict__ zbuf, int64_t zstride,
                                                int adjoint) {
-  extern __shared__ double2 z[];
+  extern __shared__ double2 sh[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int r = B.r;
   double2* vc = v + blockIdx.y * n;
   const double2* zc = zbuf + blockIdx.y * zstride + B.zoff;
+  double2* red = sh;
+  double2* z = sh + 256;        // r
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     z[k] = zc[k];
     if (it.c0 == 0) vc[B.idx[k]] = z[k];   // b_R = z, once per box
   }
   __syncthreads();
-  const int* Cidx = B.idx + r;
-  for (int i = it.c0 + threadIdx.x; i < it.c1; i += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    if (!adjoint)
-      for (int k = 0; k < r; ++k) cfma(acc, B.XCR[i + (int64_t)k * B.ldL], z[k]);
-    else
-      for (int k = 0; k < r; ++k) cfma_cj(acc, B.XRC[k + (int64_t)i * B.ldU], z[k]);
-    int dof = Cidx[i];
-    vc[dof] = csub(vc[dof], acc);
-  }
+  const int* Cidx = B.idx + r + it.c0;
+  auto st = [=](int o, double2 y) { const int dof = Cidx[o]; vc[dof] = csub(vc[dof], y); };
+  const int w = it.c1 - it.c0;
+  if (!adjoint) mv_cols<false>(B.XCR + it.c0, B.ldL, z, w, r, red, st);
+  else mv_dots<true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, z, w, r, st);
 }
 
+// backward: partial = op(X_RC)[:, chunk] x_C[chunk] (r values per chunk)
 __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                const double2* __restrict__ v, int64_t n,
@@ -229,33 +273,15 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   const int r = B.r;
   const double2* vc = v + blockIdx.y * n;
   const int w = it.c1 - it.c0;
-  double2* u = sh;            // chunk values of x_C
-  double2* red = sh + w;      // 256
+  double2* red = sh;            // 256
+  double2* u = sh + 256;        // chunk values of x_C
   const int* Cidx = B.idx + r;
   for (int j = threadIdx.x; j < w; j += blockDim.x) u[j] = vc[Cidx[it.c0 + j]];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double2* out = partial + blockIdx.y * pstride + it.part;
-  for (int kb = 0; kb < r; kb += 32) {
-    int k = kb + lane;
-    double2 acc = mk(0.0, 0.0);
-    if (k < r) {
-      if (!adjoint)
-        for (int j = warp; j < w; j += nw)
-          cfma(acc, B.XRC[k + (int64_t)(it.c0 + j) * B.ldU], u[j]);
-      else
-        for (int j = warp; j < w; j += nw)
-          cfma_cj(acc, B.XCR[(it.c0 + j) + (int64_t)k * B.ldL], u[j]);
-    }
-    red[warp * 32 + lane] = acc;
-    __syncthreads();
-    if (warp == 0 && k < r) {
-      double2 t = mk(0.0, 0.0);
-      for (int q = 0; q < nw; ++q) t = cadd(t, red[q * 32 + lane]);
-      out[k] = t;
-    }
-    __syncthreads();
-  }
+  auto st = [=](int o, double2 y) { out[o] = y; };
+  if (!adjoint) mv_cols<false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, u, r, w, red, st);
+  else mv_dots<true>(B.XCR + it.c0, B.ldL, u, r, w, st);
 }
 
 static void set_smem_attr() {
@@ -267,35 +293,37 @@ static void set_smem_attr() {
   done = true;
 }
 
+void prepare_solve_kernels() { set_smem_attr(); }
+
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
                   double2* partial, int64_t pstride, cudaStream_t st) {
   if (sg.nb <= 0) return;
   set_smem_attr();
   const int adj = adjoint ? 1 : 0;
-  const size_t base = (size_t)(256 + kRowChunk) * sizeof(double2);
+  const size_t red = 256 * sizeof(double2);
+  const size_t smr = red + (size_t)sg.rmax * sizeof(double2);
   if (!backward) {
     if (sg.smax > 0)
       FMMLU_LAUNCH("sweep_fwd", st,
-                   k_sw_y<<<dim3(sg.nri, nrhs), 256, base + sg.smax * sizeof(double2), st>>>(
+                   k_sw_y<<<dim3(sg.nri, nrhs), 256, (size_t)sg.smax * sizeof(double2), st>>>(
                        boxes, items, sg.ri0, v, n, adj));
     FMMLU_LAUNCH("sweep_fwd", st,
-                 k_sw_z<<<dim3(sg.nri, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
-                     boxes, items, sg.ri0, v, n, partial, pstride, adj));
+                 k_sw_z<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
+                                                             partial, pstride, adj));
     FMMLU_LAUNCH("sweep_fwd_c", st,
-                 k_fwd_c<<<dim3(sg.ni, nrhs), 256, (size_t)sg.rmax * sizeof(double2), st>>>(
-                     boxes, items, sg.i0, v, n, partial, pstride, adj));
+                 k_fwd_c<<<dim3(sg.ni, nrhs), 256, smr, st>>>(boxes, items, sg.i0, v, n,
+                                                             partial, pstride, adj));
   } else {
-    size_t sm1 = (size_t)(kSweepChunk + 256) * sizeof(double2);
+    const size_t sm1 = red + (size_t)sg.chunk * sizeof(double2);
     FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
                                                                                partial, pstride, adj));
     FMMLU_LAUNCH("sweep_bwd", st,
-                 k_sw_xr<<<dim3(sg.nri, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
-                     boxes, items, sg.ri0, v, n, partial, pstride, adj));
+                 k_sw_xr<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
+                                                              partial, pstride, adj));
     if (sg.nsi > 0)
       FMMLU_LAUNCH("sweep_bwd", st,
-                   k_sw_xs<<<dim3(sg.nsi, nrhs), 256, base + sg.rmax * sizeof(double2), st>>>(
-                       boxes, items, sg.si0, v, n, adj));
+                   k_sw_xs<<<dim3(sg.nsi, nrhs), 256, smr, st>>>(boxes, items, sg.si0, v, n, adj));
   }
 }
 
@@ -325,126 +353,117 @@ void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n, 
   FMMLU_LAUNCH("root_scatter", st, k_root_scatter<<<dim3((n0 + 255) / 256, nrhs), 256, 0, st>>>(vr, dofs, n0, n, v));
 }
 
-// forward step of block i: z_i = op(D_i^{-1}) b_i (every CTA recomputes it),
-// then b_later -= op(A[later, i]) z_i on this CTA's rows; z_i stored in z.
-constexpr int kRootRows = 256;
+// forward step of block i: z_i = op(D_i^{-1}) b_i (every CTA recomputes it
+// from L2), then b_later -= op(A[later, i]) z_i on this CTA's kRootRows rows;
+// z_i stored in z.
+constexpr int kRootRows = 64;
+constexpr int kRootCols = 128;
+constexpr int kRootMaxBlock = 256;
 __global__ void __launch_bounds__(256) k_root_fwd(const double2* __restrict__ A, int64_t n0, int i0,
                                                   int r, double2* __restrict__ vr,
                                                   double2* __restrict__ z, int adjoint) {
-  __shared__ double2 bi[256], zi[256];
-  int c = blockIdx.y;
+  __shared__ double2 bi[kRootMaxBlock], zi[kRootMaxBlock], red[256];
+  const int c = blockIdx.y;
   double2* vc = vr + c * n0;
   double2* zc = z + c * n0;
   for (int k = threadIdx.x; k < r; k += blockDim.x) bi[k] = vc[i0 + k];
   __syncthreads();
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int l = 0; l < r; ++l) {
-      if (!adjoint) cfma(acc, A[(i0 + k) + (i0 + l) * n0], bi[l]);
-      else cfma_cj(acc, A[(i0 + l) + (i0 + k) * n0], bi[l]);
-    }
-    zi[k] = acc;
-  }
+  const double2* D = A + i0 + (int64_t)i0 * n0;
+  double2* zip = zi;
+  auto sz = [=](int o, double2 y) { zip[o] = y; };
+  if (!adjoint) mv_cols<false>(D, n0, bi, r, r, red, sz);
+  else mv_dots<true>(D, n0, bi, r, r, sz);
   __syncthreads();
   if (blockIdx.x == 0)
     for (int k = threadIdx.x; k < r; k += blockDim.x) zc[i0 + k] = zi[k];
-  int i1 = i0 + r;
-  int row = i1 + blockIdx.x * kRootRows + threadIdx.x;
-  if (row < n0) {
-    double2 acc = mk(0.0, 0.0);
-    for (int k = 0; k < r; ++k) {
-      if (!adjoint) cfma(acc, A[row + (i0 + k) * n0], zi[k]);
-      else cfma_cj(acc, A[(i0 + k) + row * n0], zi[k]);
-    }
-    vc[row] = csub(vc[row], acc);
-  }
+  const int row0 = i0 + r + blockIdx.x * kRootRows;
+  const int nrow = min(kRootRows, (int)n0 - row0);
+  if (nrow <= 0) return;
+  auto su = [=](int o, double2 y) { vc[row0 + o] = csub(vc[row0 + o], y); };
+  if (!adjoint) mv_cols<false>(A + row0 + (int64_t)i0 * n0, n0, zi, nrow, r, red, su);
+  else mv_dots<true>(A + i0 + (int64_t)row0 * n0, n0, zi, nrow, r, su);
 }
 
-// backward, phase 1: partial[c][blk][k] = sum over this CTA's columns j of
-// op(A[i, later])[k, j] x_j ; phase 2 reduces and applies x_i = z_i - D^{-1} t.
-constexpr int kRootCols = 512;
-__global__ void __launch_bounds__(256) k_root_bwd1(const double2* __restrict__ A, int64_t n0,
-                                                   int i0, int r, const double2* __restrict__ x,
-                                                   double2* __restrict__ partial, int nblk,
-                                                   int adjoint) {
-  __shared__ double2 red[256];
-  int c = blockIdx.y;
-  const double2* xc = x + c * n0;
-  int i1 = i0 + r;
-  int j0 = i1 + blockIdx.x * kRootCols;
-  int j1 = min((int)n0, j0 + kRootCols);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int kb = 0; kb < r; kb += 32) {
-    int k = kb + lane;
-    double2 acc = mk(0.0, 0.0);
-    if (k < r)
-      for (int j = j0 + warp; j < j1; j += nw) {
-        if (!adjoint) cfma(acc, A[(i0 + k) + (int64_t)j * n0], xc[j]);
-        else cfma_cj(acc, A[j + (int64_t)(i0 + k) * n0], xc[j]);
-      }
-    red[warp * 32 + lane] = acc;
-    __syncthreads();
-    if (warp == 0 && k < r) {
-      double2 s = mk(0.0, 0.0);
-      for (int w = 0; w < nw; ++w) s = cadd(s, red[w * 32 + lane]);
-      partial[((int64_t)c * nblk + blockIdx.x) * 256 + k] = s;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(256) k_root_bwd2(const double2* __restrict__ A, int64_t n0,
-                                                   int i0, int r, double2* __restrict__ x,
-                                                   const double2* __restrict__ z,
-                                                   const double2* __restrict__ partial, int nblk,
-                                                   int adjoint) {
-  __shared__ double2 t[256];
-  int c = blockIdx.x;
+// backward step of block i: every CTA forms partial = op(A[i, later]) x_later
+// over its kRootCols columns; the last CTA to finish (one counter per
+// right-hand side, reset by that CTA) sums the partials and applies
+// x_i = z_i - op(D_i^{-1}) (sum). No CTA waits for another.
+__global__ void __launch_bounds__(256) k_root_bwd(const double2* __restrict__ A, int64_t n0,
+                                                  int i0, int r, double2* __restrict__ x,
+                                                  const double2* __restrict__ z,
+                                                  double2* __restrict__ partial, int pst,
+                                                  int* __restrict__ cnt, int adjoint) {
+  __shared__ double2 u[kRootCols], t[kRootMaxBlock], red[256];
+  __shared__ int last;
+  const int c = blockIdx.y, nblk = gridDim.x;
   double2* xc = x + c * n0;
   const double2* zc = z + c * n0;
+  const int j0 = i0 + r + blockIdx.x * kRootCols;
+  const int nj = max(0, min(kRootCols, (int)n0 - j0));
+  for (int j = threadIdx.x; j < nj; j += blockDim.x) u[j] = xc[j0 + j];
+  __syncthreads();
+  double2* pc = partial + ((int64_t)c * nblk + blockIdx.x) * pst;
+  auto sp = [=](int o, double2 y) { pc[o] = y; };
+  if (nj > 0) {
+    if (!adjoint) mv_cols<false>(A + i0 + (int64_t)j0 * n0, n0, u, r, nj, red, sp);
+    else mv_dots<true>(A + j0 + (int64_t)i0 * n0, n0, u, r, nj, sp);
+  } else {
+    for (int k = threadIdx.x; k < r; k += blockDim.x) pc[k] = mk(0.0, 0.0);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&cnt[c], 1) == nblk - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   for (int k = threadIdx.x; k < r; k += blockDim.x) {
     double2 s = mk(0.0, 0.0);
-    for (int p = 0; p < nblk; ++p) s = cadd(s, partial[((int64_t)c * nblk + p) * 256 + k]);
+    for (int p = 0; p < nblk; ++p) s = cadd(s, __ldcg(&partial[((int64_t)c * nblk + p) * pst + k]));
     t[k] = s;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int l = 0; l < r; ++l) {
-      if (!adjoint) cfma(acc, A[(i0 + k) + (i0 + l) * n0], t[l]);
-      else cfma_cj(acc, A[(i0 + l) + (i0 + k) * n0], t[l]);
-    }
-    xc[i0 + k] = csub(zc[i0 + k], acc);
-  }
+  const double2* D = A + i0 + (int64_t)i0 * n0;
+  auto sx = [=](int o, double2 y) { xc[i0 + o] = csub(zc[i0 + o], y); };
+  if (!adjoint) mv_cols<false>(D, n0, t, r, r, red, sx);
+  else mv_dots<true>(D, n0, t, r, r, sx);
+  if (threadIdx.x == 0) cnt[c] = 0;
 }
 
-void launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
-                       double2* partial, int nrhs, bool adjoint, cudaStream_t st) {
-  if (n0 <= 0) return;
-  int adj = adjoint ? 1 : 0;
+size_t root_solve_scratch_bytes(int n0, int nb, int nrhs) {
+  if (n0 <= 0) return 0;
+  const size_t nblk = std::max(1, (n0 + kRootCols - 1) / kRootCols);
+  const size_t part = ((size_t)nrhs * nblk * nb * sizeof(double2) + 255) & ~(size_t)255;
+  return part + (((size_t)nrhs * sizeof(int) + 255) & ~(size_t)255);
+}
+
+cudaError_t launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
+                              void* scratch, int nrhs, bool adjoint, cudaStream_t st) {
+  if (n0 <= 0) return cudaSuccess;
+  if (nb < 1 || nb > kRootMaxBlock) return cudaErrorInvalidValue;
+  const int adj = adjoint ? 1 : 0;
+  const size_t nblk_max = std::max(1, (n0 + kRootCols - 1) / kRootCols);
+  const size_t part_bytes = ((size_t)nrhs * nblk_max * nb * sizeof(double2) + 255) & ~(size_t)255;
+  double2* partial = static_cast<double2*>(scratch);
+  int* cnt = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + part_bytes);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nrhs * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   for (int i0 = 0; i0 < n0; i0 += nb) {
-    int r = std::min(nb, n0 - i0);
-    int later = n0 - i0 - r;
-    int nblk = std::max(1, (later + kRootRows - 1) / kRootRows);
+    const int r = std::min(nb, n0 - i0);
+    const int later = n0 - i0 - r;
+    const int nblk = std::max(1, (later + kRootRows - 1) / kRootRows);
     FMMLU_LAUNCH("root_fwd", st, k_root_fwd<<<dim3(nblk, nrhs), 256, 0, st>>>(A, n0, i0, r, vr, z, adj));
   }
-  // backward: x := z, then blocks from last to first
-  int nbl = (n0 + nb - 1) / nb;
+  // backward: blocks from last to first; x overwrites vr
+  const int nbl = (n0 + nb - 1) / nb;
   for (int bi = nbl - 1; bi >= 0; --bi) {
-    int i0 = bi * nb;
-    int r = std::min(nb, n0 - i0);
-    int later = n0 - i0 - r;
-    if (later > 0) {
-      int nblk = (later + kRootCols - 1) / kRootCols;
-      FMMLU_LAUNCH("root_bwd1", st, k_root_bwd1<<<dim3(nblk, nrhs), 256, 0, st>>>(
-                                        A, n0, i0, r, vr, partial, nblk, adj));
-      FMMLU_LAUNCH("root_bwd2", st, k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial,
-                                                                     nblk, adj));
-    } else {
-      FMMLU_LAUNCH("root_bwd2", st,
-                   k_root_bwd2<<<nrhs, 256, 0, st>>>(A, n0, i0, r, vr, z, partial, 0, adj));
-    }
+    const int i0 = bi * nb;
+    const int r = std::min(nb, n0 - i0);
+    const int later = n0 - i0 - r;
+    const int nblk = std::max(1, (later + kRootCols - 1) / kRootCols);
+    FMMLU_LAUNCH("root_bwd", st, k_root_bwd<<<dim3(nblk, nrhs), 256, 0, st>>>(
+                                     A, n0, i0, r, vr, z, partial, nb, cnt, adj));
   }
+  return cudaGetLastError();
 }
 
 }  // namespace fmmlu

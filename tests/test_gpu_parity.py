@@ -272,6 +272,67 @@ def test_multiple_rhs_and_aliasing(pkg, ell):
     assert torch.equal(inplace, xt)
 
 
+def test_solve_graph_replay_and_chunk_sizes(pkg, ell):
+    """The sweeps replayed as one CUDA graph give the eager launches' result
+    bit for bit and count the same kernels; every chunk size of the C products
+    gives the same solution up to the order of the partial sums."""
+    s, A, b, xd = ell
+    B2 = np.stack([b, np.conj(b)])
+    bt = torch.from_numpy(B2).to("cuda")
+    sols = {}
+    for chunk in (16, 64, 4096):
+        fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          solve_chunk=chunk, solve_graph=1)
+        xs, ys, counts = [], [], []
+        for _ in range(3):                 # eager, then captured, then replayed
+            l0 = pkg.fmmlu_kernel_launches()
+            x = torch.empty_like(bt)
+            y = torch.empty_like(bt)
+            pkg.fmmlu_solve(fac.handle, bt, x, s.n)
+            pkg.fmmlu_solve_adjoint(fac.handle, bt, y, s.n)
+            torch.cuda.synchronize()
+            counts.append(pkg.fmmlu_kernel_launches() - l0)
+            xs.append(x)
+            ys.append(y)
+        fac.free()
+        assert torch.equal(xs[0], xs[1]) and torch.equal(xs[0], xs[2])
+        assert torch.equal(ys[0], ys[1]) and torch.equal(ys[0], ys[2])
+        assert counts[0] == counts[1] == counts[2] > 0
+        sols[chunk] = (xs[0].cpu().numpy(), ys[0].cpu().numpy())
+    x0, y0 = sols[64]
+    for chunk, (x1, y1) in sols.items():
+        assert np.linalg.norm(x1 - x0) <= 1e-11 * np.linalg.norm(x0), chunk
+        assert np.linalg.norm(y1 - y0) <= 1e-11 * np.linalg.norm(y0), chunk
+    res = np.linalg.norm(A @ x0[0] - b) / np.linalg.norm(b)
+    assert res <= 1e-5
+
+
+def test_solve_chunk_tuner_and_cache_file(pkg, ell, tmp_path):
+    """autotune times the candidate chunks on the first solve, keeps the
+    fastest, writes it to the cache file, and reuses it for a second handle of
+    the same structure without timing again."""
+    s, A, b, xd = ell
+    path = tmp_path / "tune.txt"
+    bt = torch.from_numpy(b).to("cuda")
+    ref = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                      solve_chunk=64)
+    xr = ref.solve(bt).cpu().numpy()
+    ref.free()
+    for rep in range(2):
+        fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          autotune=1, autotune_cache=str(path))
+        x = fac.solve(bt).cpu().numpy()
+        fac.free()
+        assert np.linalg.norm(x - xr) <= 1e-11 * np.linalg.norm(xr)
+        lines = [ln.split() for ln in path.read_text().splitlines()]
+        assert len(lines) == 1
+        key, val = lines[0]
+        assert key.startswith("solve_chunk|") and key.endswith("|nrhs=1|adj=0")
+        assert int(val) in (32, 64, 128, 256)
+    with pytest.raises(pkg.FmmluError):
+        _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, solve_chunk=40)
+
+
 def test_mixed_precision_within_10eps(pkg, ell):
     s, A, b, xd = ell
     eps = 1e-4
