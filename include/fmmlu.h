@@ -126,13 +126,21 @@ typedef struct fmmlu_opts {
                                  replay the sweeps as one CUDA graph;
                                  2: capture on the first solve. Solves with
                                  opts.profile = 1 never use graphs.        */
-  int autotune;               /* 1 (default): on the first solve with a given
-                                 nrhs and direction, time the candidate
-                                 solve chunks (32, 64, 128, 256) on the
-                                 caller's right-hand sides and keep the
-                                 fastest; results are shared by all handles
-                                 with the same structure in the process.
-                                 0: use solve_chunk (or 64).               */
+  int autotune;               /* 1 (default): pick launch schedules by
+                                 timing them on the GPU, once per shape:
+                                 - the split-K chunk length of each colour's
+                                   Gram product (32, 64, 128, 256 or 4096
+                                   k16 steps; every length gives the same
+                                   exact sums), keyed by the colour's tile
+                                   count and k range (log2 buckets);
+                                 - with solve_chunk = 0, the solve chunk
+                                   (32, 64, 128, 256) on the first solve
+                                   with a given nrhs and direction, on the
+                                   caller's right-hand sides.
+                                 Results are shared by all handles in the
+                                 process (and the cache file below).
+                                 0: fixed defaults (128 steps; solve_chunk
+                                 or 64).                                  */
   const char* autotune_cache; /* NULL or a file path: tuning results are read
                                  from it (lines "key value") and appended to
                                  it, so later processes skip the timing.

@@ -221,6 +221,7 @@ struct SolveCtx {
   std::shared_ptr<SolvePlan> plan;
   DevPool mem;
   double2 *v = nullptr, *part = nullptr, *vr = nullptr, *z = nullptr;
+  int* cnt = nullptr;           // per box and right-hand side: backward chunks done
   void* rscr = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;
@@ -420,6 +421,110 @@ int status_to_code(int s, std::string& msg) {
   return 0;
 }
 
+// process-wide tuning results (key -> chunk), optionally kept in text files
+// of "key value" lines: a file is read on first use and every result this
+// process uses that the file lacks is appended to it
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+std::map<std::string, std::set<std::string>> g_tune_files;
+
+bool valid_chunk(int c) { return c >= 16 && c <= 4096 && c % 16 == 0; }
+
+std::set<std::string>& tune_file_keys(const std::string& path) {
+  auto it = g_tune_files.find(path);
+  if (it != g_tune_files.end()) return it->second;
+  std::set<std::string>& keys = g_tune_files[path];
+  std::ifstream f(path);
+  std::string k;
+  long v;
+  while (f >> k >> v)
+    if (valid_chunk((int)v)) {
+      g_tune[k] = (int)v;
+      keys.insert(k);
+    }
+  return keys;
+}
+
+bool tune_lookup(const std::string& path, const std::string& key, int* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (!path.empty()) tune_file_keys(path);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(const std::string& path, const std::string& key, int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = v;
+  if (path.empty()) return;
+  std::set<std::string>& keys = tune_file_keys(path);
+  if (keys.count(key)) return;
+  std::ofstream f(path, std::ios::app);
+  if (f) {
+    f << key << ' ' << v << '\n';
+    keys.insert(key);
+  }
+}
+
+std::string device_tag() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
+    return "unknown";
+  std::string s = pr.name;
+  for (char& ch : s)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return s + "_sm" + std::to_string(pr.major) + std::to_string(pr.minor);
+}
+
+// k16 steps per split-K chunk of a colour's Gram product. With autotune on,
+// the colour's shape (log2 buckets of its upper-triangle tiles and of its
+// longest k range) is looked up in the process-wide tuning results; on a
+// miss every candidate runs once on this colour (all give the same exact
+// sums) and the fastest is kept.
+template <class Run>
+int gram_chunk_for(const fmmlu_opts& opt, const std::vector<TcBoxSize>& bs, bool fp32,
+                   cudaStream_t st, Run&& run) {
+  if (!opt.autotune) return kGramChunkDefault;
+  int64_t tiles = 0, ks = 1;
+  for (const TcBoxSize& b : bs) {
+    const int64_t t = (b.a + 127) / 128, tn = (b.a + 31) / 32;
+    tiles += t * tn;
+    ks = std::max<int64_t>(ks, (b.kgram + 15) / 16);
+  }
+  auto lg = [](int64_t v) { int l = 0; while (v > 1) { v >>= 1; ++l; } return l; };
+  const std::string key = "gram_chunk|" + device_tag() + "|" + (fp32 ? "c64" : "c128") +
+                          "|tiles=" + std::to_string(lg(tiles)) + "|ks=" + std::to_string(lg(ks));
+  const std::string path = opt.autotune_cache ? opt.autotune_cache : "";
+  int chunk = 0;
+  if (!tune_lookup(path, key, &chunk)) {
+    ProfScope none(nullptr);
+    struct Ev {
+      cudaEvent_t e = nullptr;
+      ~Ev() { if (e) cudaEventDestroy(e); }
+    } e0, e1;
+    CK(cudaEventCreate(&e0.e));
+    CK(cudaEventCreate(&e1.e));
+    float best = INFINITY;
+    chunk = kGramChunkDefault;
+    for (int c : {32, 64, 128, 256, 4096}) {
+      CK(cudaEventRecord(e0.e, st));
+      run(c);
+      CK(cudaEventRecord(e1.e, st));
+      CK(cudaEventSynchronize(e1.e));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0.e, e1.e));
+      if (ms < best) {
+        best = ms;
+        chunk = c;
+      }
+    }
+  }
+  tune_store(path, key, chunk);
+  return chunk;
+}
+
 // Chunk items of the solve sweeps for one chunk size: per box, C = [S | N]
 // in chunks of `chunk` rows (each chunk owns r partial sums, which the first
 // chunk also uses as the box's z scratch), and R and S in chunks of
@@ -444,6 +549,8 @@ std::shared_ptr<SolvePlan> make_solve_plan(const fmmlu_handle* H, int chunk, cud
         part += sb.r;
       }
       sb.item_cnt = (int)items.size() - sb.item_beg;
+      sb.toff = (int)part;
+      part += sb.r;
     }
     sg.ni = (int)items.size() - sg.i0;
     sg.ri0 = (int)items.size();
@@ -894,14 +1001,19 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           for (int e = 0; e < cnt; ++e) bs[e] = TcBoxSize{desc[b0 + e].a, 0, 0, 0, desc[b0 + e].mmax};
           std::vector<TcUnit> units;
           TcPlan pl;
-          tc_plan(kTcGram, bs, units, pl);
-          const int fin0 = (int)units.size();
-          for (int e = 0; e < cnt; ++e) units.push_back(TcUnit{e, 0, 0, 0});
-          gram_units.upload(units, st);
-          CK(cudaMemsetAsync(d_gx + gx_col_off[sgi], 0,
-                             (size_t)gx_col_len[sgi] * sizeof(unsigned long long), st));
-          launch_tc_planned(kTcGram, LD, b0, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g,
-                            H->fp32, gram_units.d, pl, st, d_gx, d_gx_off);
+          int fin0 = 0;
+          auto gram_product = [&](int chunk) {
+            units.clear();
+            tc_plan(kTcGram, bs, units, pl, chunk);
+            fin0 = (int)units.size();
+            for (int e = 0; e < cnt; ++e) units.push_back(TcUnit{e, 0, 0, 0});
+            gram_units.upload(units, st);
+            CK(cudaMemsetAsync(d_gx + gx_col_off[sgi], 0,
+                               (size_t)gx_col_len[sgi] * sizeof(unsigned long long), st));
+            launch_tc_planned(kTcGram, LD, b0, d_gtb + b0, d_gr_slices, d_gr_expo, d_gbh, d_gr_g,
+                              H->fp32, gram_units.d, pl, st, d_gx, d_gx_off);
+          };
+          gram_product(gram_chunk_for(opt, bs, H->fp32, st, gram_product));
           launch_gram_finalize(LD, b0, gram_units.d + fin0, cnt, amax, d_gtb + b0, d_gr_expo, d_gbh,
                                d_gr_g, d_gx, d_gx_off, H->fp32, st);
         } else
@@ -1254,10 +1366,15 @@ std::shared_ptr<SolvePlan> get_plan(const fmmlu_handle* H, int chunk, cudaStream
   return P;
 }
 
+size_t counter_bytes(const fmmlu_handle* H, int nrhs) {
+  return (H->sboxes.size() * (size_t)nrhs + 1) * sizeof(int);
+}
+
 void alloc_ctx(const fmmlu_handle* H, SolveCtx& c) {
   const int64_t n = H->n;
   c.v = c.mem.get<double2>((size_t)n * c.nrhs);
   c.part = c.mem.get<double2>((size_t)c.plan->part_max * c.nrhs);
+  c.cnt = c.mem.get<int>(counter_bytes(H, c.nrhs) / sizeof(int));
   if (H->n0 > 0) {
     c.vr = c.mem.get<double2>((size_t)H->n0 * c.nrhs);
     c.z = c.mem.get<double2>((size_t)H->n0 * c.nrhs);
@@ -1269,15 +1386,18 @@ void alloc_ctx(const fmmlu_handle* H, SolveCtx& c) {
 void run_sweeps(const fmmlu_handle* H, const SolveCtx& c, cudaStream_t st) {
   const SolvePlan& P = *c.plan;
   const int64_t n = H->n, pst = P.part_max;
+  CK(cudaMemsetAsync(c.cnt, 0, counter_bytes(H, c.nrhs), st));
   for (const auto& sg : P.segs)
-    launch_sweep(P.d_boxes, P.d_items, sg, c.v, n, c.nrhs, false, c.adjoint, c.part, pst, st);
+    launch_sweep(P.d_boxes, P.d_items, sg, c.v, n, c.nrhs, false, c.adjoint, c.part, pst, st,
+                 c.cnt);
   if (H->n0 > 0) {
     launch_root_gather(c.v, H->d_root_dofs, H->n0, n, c.nrhs, c.vr, st);
     CK(launch_root_solve(H->d_root, H->n0, H->nb_root, c.vr, c.z, c.rscr, c.nrhs, c.adjoint, st));
     launch_root_scatter(c.vr, H->d_root_dofs, H->n0, n, c.nrhs, c.v, st);
   }
   for (auto it = P.segs.rbegin(); it != P.segs.rend(); ++it)
-    launch_sweep(P.d_boxes, P.d_items, *it, c.v, n, c.nrhs, true, c.adjoint, c.part, pst, st);
+    launch_sweep(P.d_boxes, P.d_items, *it, c.v, n, c.nrhs, true, c.adjoint, c.part, pst, st,
+                 c.cnt);
 }
 
 // Record the sweeps of c into a CUDA graph on the handle's own capture stream
@@ -1325,63 +1445,6 @@ SolveCtx* get_ctx(const fmmlu_handle* H, int nrhs, bool adjoint, cudaStream_t st
   CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
   H->ctxs.push_back(std::move(c));
   return H->ctxs.back().get();
-}
-
-// process-wide tuning results (key -> chunk), optionally kept in text files
-// of "key value" lines: a file is read on first use and every result this
-// process uses that the file lacks is appended to it
-std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
-std::map<std::string, std::set<std::string>> g_tune_files;
-
-bool valid_chunk(int c) { return c >= 16 && c <= 4096 && c % 16 == 0; }
-
-std::set<std::string>& tune_file_keys(const std::string& path) {
-  auto it = g_tune_files.find(path);
-  if (it != g_tune_files.end()) return it->second;
-  std::set<std::string>& keys = g_tune_files[path];
-  std::ifstream f(path);
-  std::string k;
-  long v;
-  while (f >> k >> v)
-    if (valid_chunk((int)v)) {
-      g_tune[k] = (int)v;
-      keys.insert(k);
-    }
-  return keys;
-}
-
-bool tune_lookup(const std::string& path, const std::string& key, int* out) {
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  if (!path.empty()) tune_file_keys(path);
-  auto it = g_tune.find(key);
-  if (it == g_tune.end()) return false;
-  *out = it->second;
-  return true;
-}
-
-void tune_store(const std::string& path, const std::string& key, int v) {
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[key] = v;
-  if (path.empty()) return;
-  std::set<std::string>& keys = tune_file_keys(path);
-  if (keys.count(key)) return;
-  std::ofstream f(path, std::ios::app);
-  if (f) {
-    f << key << ' ' << v << '\n';
-    keys.insert(key);
-  }
-}
-
-std::string device_tag() {
-  int dev = 0;
-  cudaDeviceProp pr{};
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
-    return "unknown";
-  std::string s = pr.name;
-  for (char& ch : s)
-    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
-  return s + "_sm" + std::to_string(pr.major) + std::to_string(pr.minor);
 }
 
 // Time the whole solve (both sweeps and the root) once per candidate chunk on
@@ -1751,7 +1814,8 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
     const size_t br = round256((size_t)16 * n0 * nrhs);
     const size_t bp = round256(root_solve_scratch_bytes(n0, h->nb_root, nrhs));
     const size_t bs = round256((size_t)16 * nrhs * plan->part_max);
-    const size_t need = bv + 2 * br + bp + bs;
+    const size_t bc = round256(counter_bytes(h, nrhs));
+    const size_t need = bv + 2 * br + bp + bs + bc;
     if (need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
       throw Error(FMMLU_ERR_LIMIT,
                   "fmmlu_solve_noalloc needs " + std::to_string(need) +
@@ -1767,6 +1831,7 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
     c.z = reinterpret_cast<double2*>(base + bv + br);
     c.rscr = base + bv + 2 * br;
     c.part = reinterpret_cast<double2*>(base + bv + 2 * br + bp);
+    c.cnt = reinterpret_cast<int*>(base + bv + 2 * br + bp + bs);
     launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, c.v, st);
     run_sweeps(h, c, st);
     launch_scatter_vec(c.v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);

@@ -105,6 +105,7 @@ constexpr int kNsMin = 32;      // smallest r refined on the tensor cores
 // one per eliminated box, in elimination order (solve plan)
 struct SolveBox {
   int r, s, n, zoff;       // zoff: the box's r scratch values (its first chunk's partials)
+  int toff;                // r values: the summed partials of the backward sweep
   int item_beg, item_cnt;  // chunks of C = [S | N] (SweepItem list)
   const int* idx;          // [R | S | N]
   const double2* T;  int ldT;
@@ -239,7 +240,8 @@ enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5, kT
        kTcNsX = 7, kTcRootW = 8, kTcRootS = 9 };
 struct TcUnit {          // one CTA of a tcgen05-path launch
   int box;               // box index relative to the colour's first box
-  int side;              // 0 = A operand, 1 = B operand (split launches)
+  int side;              // 0 = A operand, 1 = B operand (split launches); product
+                         // units of a split-K problem: k16 steps per chunk
   int x, y;              // row block and k group (split) or tile (product)
 };
 struct TcBoxSize {       // exact (or bounding) sizes of one box on the host
@@ -249,8 +251,11 @@ struct TcBoxSize {       // exact (or bounding) sizes of one box on the host
 struct TcPlan {          // the five launches of one problem: offsets into the unit list
   int off[5], cnt[5];    // exponents A, B; digits A, B; product tiles
 };
+// gram_chunk: k16 steps per split-K chunk of the Gram product (kTcGram only;
+// every chunk length gives the same exact sums)
+constexpr int kGramChunkDefault = 128;
 void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>& units,
-             TcPlan& plan);
+             TcPlan& plan, int gram_chunk = kGramChunkDefault);
 void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_tb, void* slices,
                        int* expo, const GramBoxHost* d_gb, double2* gbuf, bool fp32,
                        const TcUnit* d_units, const TcPlan& pl, cudaStream_t st,
@@ -301,9 +306,10 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs,
                         double2* x, cudaStream_t st);
 // one-time kernel attributes of the sweeps (call before a stream capture)
 void prepare_solve_kernels();
+// cnt: one int per eliminated box and right-hand side, zero between sweeps
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
-                  double2* partial, int64_t pstride, cudaStream_t st);
+                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt);
 void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n,
                         int nrhs, double2* vr, cudaStream_t st);
 void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,

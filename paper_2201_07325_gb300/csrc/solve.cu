@@ -111,13 +111,14 @@ __device__ __forceinline__ void mv_cols(const double2* __restrict__ M, int64_t l
 }
 
 // store(o, y_o) with y_o = sum_{q < nq} op(M[q + o ld]) x[q], o < no: every
-// output is a dot product along a contiguous column. A group of 8, 16 or 32
-// lanes (by nq) per output, shuffle reduction inside the group.
+// output is a dot product along a contiguous column. A group of 4 to 32 lanes
+// per output, sized so that every lane takes at least four terms (the
+// shuffle reduction inside the group costs fp64 adds of its own).
 template <bool kCj, class Store>
 __device__ __forceinline__ void mv_dots(const double2* __restrict__ M, int64_t ld,
                                         const double2* x, int no, int nq, Store store) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int sw = nq > 16 ? 32 : (nq > 8 ? 16 : 8);
+  const int sw = nq >= 128 ? 32 : (nq >= 64 ? 16 : (nq >= 32 ? 8 : 4));
   const int per = 32 / sw;
   const int sl = lane % sw, sub = lane / sw;
   for (int ob = w * per; ob < no; ob += nw * per) {
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes
             [=](int o, double2 z) { zo[o] = z; });
 }
 
-// backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = sum of the partials
+// backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = the summed partials
 __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
@@ -204,11 +205,7 @@ __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxe
   const double2* pc = partial + blockIdx.y * pstride;
   double2* red = sh;
   double2* tt = sh + 256;       // r
-  for (int k = threadIdx.x; k < B.r; k += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int q = B.item_beg; q < B.item_beg + B.item_cnt; ++q) acc = cadd(acc, pc[items[q].part + k]);
-    tt[k] = acc;
-  }
+  for (int k = threadIdx.x; k < B.r; k += blockDim.x) tt[k] = pc[B.toff + k];
   __syncthreads();
   const int* Ridx = B.idx + it.c0;
   xinv_rows(B, it.c0, it.c1 - it.c0, tt, red, adjoint != 0, [=](int o, double2 y) {
@@ -261,12 +258,16 @@ __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxe
   else mv_dots<true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, z, w, r, st);
 }
 
-// backward: partial = op(X_RC)[:, chunk] x_C[chunk] (r values per chunk)
+// backward: partial = op(X_RC)[:, chunk] x_C[chunk] (r values per chunk);
+// the last chunk of a box to finish (one counter per box and right-hand
+// side, reset by that CTA; no CTA waits) sums the box's partials in chunk
+// order into its t slots
 __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                const double2* __restrict__ v, int64_t n,
                                                double2* __restrict__ partial, int64_t pstride,
-                                               int adjoint) {
+                                               int* __restrict__ cnt, int adjoint) {
+  __shared__ int last;
   extern __shared__ double2 sh[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
@@ -282,6 +283,46 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   auto st = [=](int o, double2 y) { out[o] = y; };
   if (!adjoint) mv_cols<false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, u, r, w, red, st);
   else mv_dots<true>(B.XCR + it.c0, B.ldL, u, r, w, st);
+  int* ctr = cnt + (int64_t)it.box * gridDim.y + blockIdx.y;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ctr, 1) == B.item_cnt - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // t[k] = sum_j partial_j[k]: threads over k (rp of them) and over
+  // interleaved groups of j, four loads in flight each, groups summed in a
+  // fixed order (the result does not depend on which CTA came last)
+  const double2* pb = partial + blockIdx.y * pstride + B.zoff;
+  double2* tb = partial + blockIdx.y * pstride + B.toff;
+  const int nc = B.item_cnt, t = threadIdx.x;
+  const int rp = r <= 32 ? 32 : (r <= 64 ? 64 : (r <= 128 ? 128 : 256));
+  const int G = 256 / rp, g = t / rp;
+  for (int kb = 0; kb < r; kb += rp) {
+    const int k = kb + t % rp;
+    double2 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+    if (k < r) {
+      int j = g;
+      for (; j + 3 * G < nc; j += 4 * G) {
+        const double2 p0 = __ldcg(pb + (int64_t)j * r + k);
+        const double2 p1 = __ldcg(pb + (int64_t)(j + G) * r + k);
+        const double2 p2 = __ldcg(pb + (int64_t)(j + 2 * G) * r + k);
+        const double2 p3 = __ldcg(pb + (int64_t)(j + 3 * G) * r + k);
+        a0 = cadd(a0, cadd(p0, p2));
+        a1 = cadd(a1, cadd(p1, p3));
+      }
+      for (; j < nc; j += G) a0 = cadd(a0, __ldcg(pb + (int64_t)j * r + k));
+    }
+    red[t] = cadd(a0, a1);
+    __syncthreads();
+    if (g == 0 && k < r) {
+      double2 sum = red[t];
+      for (int gg = 1; gg < G; ++gg) sum = cadd(sum, red[gg * rp + t]);
+      tb[k] = sum;
+    }
+    __syncthreads();
+  }
+  if (t == 0) *ctr = 0;
 }
 
 static void set_smem_attr() {
@@ -297,7 +338,7 @@ void prepare_solve_kernels() { set_smem_attr(); }
 
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
-                  double2* partial, int64_t pstride, cudaStream_t st) {
+                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt) {
   if (sg.nb <= 0) return;
   set_smem_attr();
   const int adj = adjoint ? 1 : 0;
@@ -317,7 +358,7 @@ void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg&
   } else {
     const size_t sm1 = red + (size_t)sg.chunk * sizeof(double2);
     FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
-                                                                               partial, pstride, adj));
+                                                                               partial, pstride, cnt, adj));
     FMMLU_LAUNCH("sweep_bwd", st,
                  k_sw_xr<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
                                                               partial, pstride, adj));

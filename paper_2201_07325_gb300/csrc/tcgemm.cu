@@ -434,7 +434,7 @@ struct TcGram {
 
 // The Gram matrix's k range (the rows of M, thousands) is split into chunks
 // of 128 k16 steps so that small colours still fill the GPU.
-template <typename CM> struct TcSplit<TcGram<CM>> { static constexpr int steps = 128; };
+template <typename CM> struct TcSplit<TcGram<CM>> { static constexpr int steps = kGramChunkDefault; };
 
 // G from the split-K int64 accumulator: G_ij = X_hi 2^(E-32) + X_lo 2^(E-16-8 DMAX)
 // for i <= j, mirrored to G_ji = conj(G_ij)
@@ -683,9 +683,12 @@ __device__ __forceinline__ TcTile tc_tile(const LevelDev& L, int b0, const TcUni
   T.k0 = 0;
   T.KS = T.KSall;
   if (TcSplit<Prob>::steps > 0) {
-    T.k0 = u.y * TcSplit<Prob>::steps;
+    // chunk length: from the unit (product units of a split-K problem carry
+    // it in `side`), else the problem's default
+    const int cs = u.side > 0 ? u.side : TcSplit<Prob>::steps;
+    T.k0 = u.y * cs;
     if (T.k0 >= T.KSall) return T;   // past the end of this box's k range
-    T.KS = min(TcSplit<Prob>::steps, T.KSall - T.k0);
+    T.KS = min(cs, T.KSall - T.k0);
   }
   T.ok = true;
   return T;
@@ -941,14 +944,14 @@ static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) 
   }
   return false;
 }
-constexpr int kGramChunk = 128;   // = TcSplit<TcGram>::steps
 
 static bool tc_kcontig(int which, bool side_b) {
   return side_b || which == kTcG1 || which == kTcGram;
 }
 
 void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>& units,
-             TcPlan& plan) {
+             TcPlan& plan, int gram_chunk) {
+  if (gram_chunk < 1) gram_chunk = kGramChunkDefault;
   for (int l = 0; l < 5; ++l) {
     plan.off[l] = (int)units.size();
     for (int e = 0; e < (int)boxes.size(); ++e) {
@@ -967,11 +970,12 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
           for (int y = 0; y < kg; ++y) units.push_back(TcUnit{e, l - 2, x, y});
       } else {                           // product tiles (and k chunks of the Gram matrix)
         const int tms = lpa / tc::kRows, tns = lpb / tc::kCols;
-        const int nchunk = which == kTcGram ? ((k + 15) / 16 + kGramChunk - 1) / kGramChunk : 1;
+        const int nchunk = which == kTcGram ? ((k + 15) / 16 + gram_chunk - 1) / gram_chunk : 1;
+        const int cs = which == kTcGram ? gram_chunk : 0;
         for (int t = 0; t < tms * tns; ++t) {
           const int i0 = (t % tms) * tc::kRows, j0 = (t / tms) * tc::kCols;
           if (which == kTcGram && j0 + tc::kCols - 1 < i0) continue;
-          for (int c = 0; c < nchunk; ++c) units.push_back(TcUnit{e, 0, t, c});
+          for (int c = 0; c < nchunk; ++c) units.push_back(TcUnit{e, cs, t, c});
         }
       }
     }

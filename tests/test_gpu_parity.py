@@ -325,12 +325,36 @@ def test_solve_chunk_tuner_and_cache_file(pkg, ell, tmp_path):
         fac.free()
         assert np.linalg.norm(x - xr) <= 1e-11 * np.linalg.norm(xr)
         lines = [ln.split() for ln in path.read_text().splitlines()]
-        assert len(lines) == 1
-        key, val = lines[0]
-        assert key.startswith("solve_chunk|") and key.endswith("|nrhs=1|adj=0")
+        solve = [ln for ln in lines if ln[0].startswith("solve_chunk|")]
+        assert len(solve) == 1
+        key, val = solve[0]
+        assert key.endswith("|nrhs=1|adj=0")
         assert int(val) in (32, 64, 128, 256)
     with pytest.raises(pkg.FmmluError):
         _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, solve_chunk=40)
+
+
+def test_gram_chunk_tuning_is_exact(pkg, ell, tmp_path):
+    """Every split-K chunk length of the Gram product adds the same exact
+    integer digit products, so the factorization with the tuned chunk lengths
+    equals the one with the fixed default bit for bit; the tuned choices go
+    to the cache file."""
+    s, A, b, xd = ell
+    path = tmp_path / "tune.txt"
+    bt = torch.from_numpy(b).to("cuda")
+    xs = []
+    for tune in (0, 1):
+        fac = _gpu_factor(pkg, s, K, 1e-6, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          solve_chunk=64, autotune=tune,
+                          autotune_cache=str(path) if tune else None)
+        xs.append(fac.solve(bt))
+        fac.free()
+    torch.cuda.synchronize()
+    assert torch.equal(xs[0], xs[1])
+    lines = [ln.split() for ln in path.read_text().splitlines()]
+    gram = [(key, int(val)) for key, val in lines if key.startswith("gram_chunk|")]
+    assert gram and all(v in (32, 64, 128, 256, 4096) for _, v in gram)
+    assert len({key for key, _ in gram}) == len(gram)
 
 
 def test_mixed_precision_within_10eps(pkg, ell):
