@@ -91,9 +91,11 @@ typedef struct fmmlu_opts {
                                  (reported by fmmlu_stats). Default 0.      */
   int cpqr_single;            /* 1: run every pivoted QR with one CTA per box
                                  (no row distribution). Default 0.          */
-  int schur_emulation;        /* products of the elimination (G1, G3, W,
-                                 Schur update) with an inner dimension >= 32,
-                                 and the Gram matrix of the ID:
+  int schur_emulation;        /* products of the elimination (G1, G3, X_RR,
+                                 W, Schur update) and of the root, and the
+                                 Gram matrix of the ID (inner dimension
+                                 >= 4 in mode 1, >= 32 in mode 2; smaller
+                                 ones run on fp64 FMA):
                                  1 (default): tcgen05 tensor cores (TMEM
                                  accumulators) on an exact split of each
                                  complex128 operand into 7 bf16 digits; every

@@ -1060,8 +1060,14 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
       const int kskip = use_tc ? kTcInnerMin : use_oz ? kOzInnerMin : 0;
-      launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
-      launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
+      // the fp64 FMA products take the boxes whose inner dimension is below
+      // kskip; with the tcgen05 path (kskip = 1) only empty products are
+      // left for G1, G3, W and the Schur update
+      const bool fma_left = kskip != 1;
+      if (fma_left) {
+        launch_gemm_g1(LD, b0, cnt, amax, nmaxm, st, kskip);
+        launch_gemm_g3(LD, b0, cnt, amax, nmaxm, st, kskip);
+      }
       if (use_tc) {
         launch_tc_planned(kTcG1, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
                           false, elim_units.d, epl[kTcG1], st);
@@ -1071,6 +1077,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 0, st);
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 1, st);
       }
+      // (X_RR of a box with no skeleton, s = 0, is still copied here)
       launch_gemm_xrr(LD, b0, cnt, amax, st, use_tc ? kTcInnerMin : 0);
       if (use_tc)
         launch_tc_planned(kTcXrr, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
@@ -1113,13 +1120,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           launch_xrr_inverse(LD, b0, cnt, amax, st);
         }
       }
-      launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
+      if (fma_left) launch_gemm_w(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc)
         launch_tc_planned(kTcW, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
                           false, elim_units.d, epl[kTcW], st);
       else if (use_oz)
         launch_oz_elim_gemms(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, 2, st);
-      launch_schur_update(LD, b0, cnt, amax, nmaxm, st, kskip);
+      if (fma_left) launch_schur_update(LD, b0, cnt, amax, nmaxm, st, kskip);
       if (use_tc)
         launch_tc_planned(kTcSchur, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
                           false, elim_units.d, epl[kTcSchur], st);

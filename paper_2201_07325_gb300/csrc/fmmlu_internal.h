@@ -206,7 +206,7 @@ void launch_oz_schur(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, v
 void launch_oz_elim_gemms(const LevelDev& L, int b0, int nb, const OzBoxHost* d_oz, void* slices,
                           int* expo, int amax, int nmax_max, int which, cudaStream_t st);
 constexpr int kOzInnerMin = 32;   // inner dimension from which the mma.sync path is used
-constexpr int kTcInnerMin = 16;   // inner dimension from which the tcgen05 path is used
+constexpr int kTcInnerMin = 1;    // inner dimension from which the tcgen05 path is used
 // Gram form of the ID (ozaki.cu, pchol.cu): G = M^H M of the ID matrix on the
 // tensor cores, then greedy pivoted Cholesky of G -- the same column selection
 // and the same R (up to row phases) as CPQR of M in exact arithmetic.
