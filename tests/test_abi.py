@@ -56,3 +56,45 @@ def test_host_side_argument_checks(lib):
     bad = pkg.fmmlu_default_opts(proxy_radius_factor=0.9)
     rc = lib.fmmlu_build_tree(ctypes.c_void_p(8), 10, ctypes.byref(bad), None, ctypes.byref(out))
     assert rc == -1 and "proxy_radius_factor" in pkg.fmmlu_last_error()
+
+
+def test_python_opts_layout_matches_the_header(tmp_path):
+    """The ctypes mirror of fmmlu_opts has the C struct's size and field
+    offsets (a C program compiled against include/fmmlu.h prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2201_07325_gb300.binding import fmmlu_opts
+    fields = [f for f, _ in fmmlu_opts._fields_]
+    prog = tmp_path / "layout.c"
+    body = "\n".join(f'  printf("{f} %zu\\n", offsetof(fmmlu_opts, {f}));' for f in fields)
+    prog.write_text(
+        "#include <stddef.h>\n#include <stdio.h>\n#include <stdint.h>\n"
+        f'#include "{HEADER}"\n'
+        "int main(void) {\n"
+        '  printf("sizeof %zu\\n", sizeof(fmmlu_opts));\n'
+        f"{body}\n  return 0;\n}}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(prog)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert int(out["sizeof"]) == ctypes.sizeof(fmmlu_opts)
+    for f in fields:
+        assert int(out[f]) == getattr(fmmlu_opts, f).offset, f
+
+
+def test_solve_and_tuning_options(lib):
+    import paper_2201_07325_gb300 as pkg
+    o = pkg.fmmlu_default_opts()
+    assert o.solve_chunk == 0 and o.solve_graph == 1 and o.autotune == 1
+    assert o.autotune_cache is None
+    out = ctypes.c_void_p()
+    for field, value in (("solve_chunk", 40), ("solve_chunk", 8192), ("solve_graph", 3),
+                         ("autotune", 2), ("schur_emulation", 3), ("id_method", -1)):
+        bad = pkg.fmmlu_default_opts(**{field: value})
+        rc = lib.fmmlu_build_tree(ctypes.c_void_p(8), 10, ctypes.byref(bad), None,
+                                  ctypes.byref(out))
+        assert rc == -1, (field, value)
+    ok = pkg.fmmlu_default_opts(autotune_cache="/nonexistent/dir/tune.txt", solve_chunk=4096)
+    assert ok.autotune_cache == b"/nonexistent/dir/tune.txt"
