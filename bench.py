@@ -485,6 +485,69 @@ def factor_once(args) -> dict:
             "kernels": st["kernels"]}
 
 
+def scaling(args) -> list:
+    """Factor and solve times against N on the ellipsoid (1, 2, 0.5) family
+    at a fixed number of points per wavelength (k = 2 pi sqrt(N / 50,000),
+    the regime of the paper's Table 2), plain fp64 at eps = 1e-6 and mixed at
+    eps = 1e-4. Per size: one factorization to warm up (and tune), then one
+    timed factorization; the solve is the mean of 5 graph replays after 3
+    warm-up solves; residual by the dense on-the-fly product up to 100,000
+    points."""
+    import time
+    import torch
+    import paper_2201_07325_gb300 as pkg
+    pkg.load_library()
+    st = torch.cuda.current_stream()
+    out = []
+    sizes = [int(v) for v in args.sizes.split(",")]
+    for prec_name, prec, eps in (("fp64", pkg.PRECISION_FP64, 1e-6),
+                                 ("mixed", pkg.PRECISION_MIXED, 1e-4)):
+        for n in sizes:
+            s = synth.make_surface("ellipsoid50k", n)
+            k = 2.0 * np.pi * float(np.sqrt(n / 50000.0))
+            b = synth.make_rhs("ellipsoid50k", s, k)
+            pts, nrm, w = (torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                           for a in (s.points, s.normals, s.weights))
+            bt = torch.from_numpy(b).cuda()
+            x = torch.empty_like(bt)
+            opts = pkg.fmmlu_default_opts(precision=prec)
+            for it in range(2):
+                t = pkg.fmmlu_build_tree(pts, opts)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = pkg.fmmlu_factor(t, pts, nrm, w, k, eps, opts)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                pkg.fmmlu_free(t)
+                if it == 0:
+                    pkg.fmmlu_free(h)
+            for _ in range(3):
+                pkg.fmmlu_solve(h, bt, x, n)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(5):
+                pkg.fmmlu_solve(h, bt, x, n)
+            e1.record(st)
+            torch.cuda.synchronize()
+            stats = pkg.fmmlu_stats(h)
+            row = {"n": n, "k": k, "precision": prec_name, "eps": eps,
+                   "factor_s": t1 - t0, "solve_ms": e0.elapsed_time(e1) / 5,
+                   "n0": stats["n0"], "factor_bytes": stats["factor_bytes"]}
+            if n <= 100000:
+                y = torch.empty_like(x)
+                pkg.fmmlu_matvec(pts, nrm, w, k, k, x, y)
+                row["residual"] = float(torch.linalg.vector_norm(y - bt)
+                                        / torch.linalg.vector_norm(bt))
+            pkg.fmmlu_free(h)
+            print(json.dumps(row), flush=True)
+            out.append(row)
+            del pts, nrm, w, bt, x
+            torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,11 +562,18 @@ def main():
                          "prints the per-kernel algorithmic flops/bytes")
     ap.add_argument("--n", type=int, default=None,
                     help="with --factor-once: the same surface family at n points")
+    ap.add_argument("--scaling", action="store_true",
+                    help="factor and solve times against N (ellipsoid family, fixed points "
+                         "per wavelength), one JSON line per size and precision")
+    ap.add_argument("--sizes", default="12500,25000,50000,100000,200000,400000")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.factor_once:
         print(json.dumps(factor_once(args)))
+        return
+    if args.scaling:
+        scaling(args)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
