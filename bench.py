@@ -174,6 +174,17 @@ def recorded_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest value of x over all ranks (the slowest replica's time);
+    x itself when there is no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, rank, world):
     import torch
     import paper_2201_07325_gb300 as pkg
@@ -265,11 +276,7 @@ def run_gpu(args, rank, world):
             pkg.fmmlu_free(h)
     launches = pkg.fmmlu_kernel_launches() - launches0
     clocks = sampler.stop()
-    step_ms = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(total_ms / args.steps, dist, dev)
     value = n * world / (step_ms / 1e3)
 
     # residual of the last solution (dense on-the-fly product, outside timing)
@@ -330,11 +337,7 @@ def run_gpu(args, rank, world):
         barrier()
         e2e_ms += e0.elapsed_time(e1)
         pkg.fmmlu_free(h)
-    e2e_ms /= e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms / e2e_steps, dist, dev)
     h2d = sum(a.numel() * a.element_size() for a in hp) + hb.numel() * hb.element_size()
     d2h = 2 * hb.numel() * hb.element_size()
 
