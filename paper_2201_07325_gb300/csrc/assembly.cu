@@ -93,20 +93,20 @@ void launch_gather_rows(const LevelDev& L, int b0, int nb, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 
-constexpr int kIdRows = 64;   // half-rows per block (pairs of rows)
+constexpr int kIdRows = 64;   // most half-rows per block (pairs of rows)
 
 // The rows come in pairs that share a kernel evaluation: row i < nq (A(q_i, b_j),
 // outgoing ring) and row nq + i (A(b_j, q_i), incoming ring, the transpose
 // block); proxy row 2nq + l (K(y_l, b_j)) and 2nq + np + l (G(b_j, y_l)).
 template <typename C>
-__global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
+__global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
   using R = decltype(C().x);
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const int nq = L.run[b].nq;
   const int np = L.n_proxy;
   const int half = nq + np;
-  const int row0 = blockIdx.x * kIdRows;
+  const int row0 = blockIdx.x * rpb;
   if (row0 >= half) return;
   const int a = d.a;
   const int* qdof = L.rows + d.rows_off;
@@ -116,7 +116,7 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
   C* M = reinterpret_cast<C*>(L.Mbuf) + d.M_off;
   const double rho = L.proxy_factor * 0.86602540378443864676 * d.h;
   const double cg = sqrt(4.0 * kPi * rho * rho / np);
-  const int rows = min(kIdRows, half - row0);
+  const int rows = min(rpb, half - row0);
   const R kk = (R)g.k, ee = (R)g.eta;
   for (int e = threadIdx.x; e < rows * a; e += blockDim.x) {
     const int i = row0 + e % rows;
@@ -166,11 +166,24 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0) {
 void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, int mmax_max,
                         bool fp32, cudaStream_t st) {
   if (nb <= 0) return;
-  dim3 grid((mmax_max / 2 + kIdRows - 1) / kIdRows, nb);   // m = 2 (nq + np) rows, in pairs
+  // m = 2 (nq + np) rows, in pairs. Every entry is computed the same way for
+  // any blocking, so colours with few boxes get shorter row blocks: the
+  // kernel is fp64-bound per SM and needs every SM busy.
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 148;
+  }
+  const int half = mmax_max / 2;
+  int rpb = kIdRows;
+  while (rpb > 8 && (int64_t)((half + rpb - 1) / rpb) * nb < 4 * (int64_t)sms) rpb >>= 1;
+  dim3 grid((half + rpb - 1) / rpb, nb);
   if (fp32)
-    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0));
+    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0, rpb));
   else
-    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<double2><<<grid, 256, 0, st>>>(L, g, b0));
+    FMMLU_LAUNCH("assemble_id", st, k_assemble_id<double2><<<grid, 256, 0, st>>>(L, g, b0, rpb));
 }
 
 // ---------------------------------------------------------------------------
