@@ -221,3 +221,22 @@ def test_planted_proxy_inside_box_is_caught(ell):
     F, rec = _factor(ell, 1e-4, proxy_factor=0.5)
     worst, _ = _id_error_ratio(rec, 1e-4)
     assert worst > 10.0
+
+
+def test_proxy_sphere_near_the_far_boundary(ell):
+    """Cross-check of the proxy radius reading: a sphere of 2.8 x the
+    half-diagonal (2.42 h, just inside the 2.5 h ball that P never enters)
+    gives IDs that still meet 10 eps against the explicit far field, a
+    solution within 10 eps, and skeleton totals close to those of the
+    default 1.5 x half-diagonal sphere."""
+    s, A, b, xd, T = ell
+    eps = 1e-4
+    F, rec = _factor(ell, eps, proxy_factor=2.8)
+    worst, count = _id_error_ratio(rec, eps)
+    assert count > 20 and worst <= 10.0
+    x = rss.solve(F, b)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 10 * eps
+    F15, rec15 = _factor(ell, eps)
+    s28 = sum(r["S"].size for r in rec)
+    s15 = sum(r["S"].size for r in rec15)
+    assert abs(s28 - s15) <= 0.15 * s15
