@@ -123,6 +123,25 @@ def test_analytic_point_source_sphere():
     assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-12
 
 
+def test_analytic_accuracy_metric_as_printed():
+    """The accuracy measure of Sec. 6.1 divides the target-error norm by
+    the L2 norm of the density on the surface, sqrt(int |sigma|^2 da), which
+    the scaled unknowns give as ||x||_2 (x = sqrt(w) sigma). Both that
+    measure and the plain relative error fall at first order in h."""
+    out = []
+    for n in (1000, 4000):
+        s = synth.sphere_fibonacci(n)
+        e_rel, A, x, b = _analytic_error(s, 1.0, (0.1, 0.2, -0.1))
+        t = synth.exterior_targets(50, 3.0)
+        u = kernel.potential(t, s.points, s.normals, s.weights, 1.0, 1.0, x)
+        ue = synth.point_source_field(t, (0.1, 0.2, -0.1), 1.0)
+        e_a = np.linalg.norm(u - ue) / np.linalg.norm(x)
+        out.append((e_rel, e_a))
+    (r1, a1), (r2, a2) = out
+    assert a1 < 0.02 and a2 < 0.01
+    assert a1 / a2 > 1.6 and r1 / r2 > 1.6
+
+
 def test_analytic_point_source_ellipsoid():
     s = synth.ellipsoid_uniform(3000, (1.0, 2.0, 0.5), seed=11)
     e, *_ = _analytic_error(s, 2.0, (0.2, 0.5, 0.05))
