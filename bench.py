@@ -432,12 +432,35 @@ def oracle_step(workload: str, nsample: int = SAMPLE_N):
     return time.perf_counter() - t0, nsample
 
 
+def single_core_oracle(workload: str, nsample: int = SAMPLE_N):
+    """The oracle step in a child process limited to one thread (the paper's
+    single-core setting); None when the child fails."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = ("import json, bench; s, p = bench.oracle_step(%r, %d); print(json.dumps([s, p]))"
+            % (workload, nsample))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                           text=True, timeout=300)
+        sec, pts = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": pts / sec, "unit": UNIT, "cores": 1,
+            "sample": f"oracle on {pts} points, one thread: {sec:.1f} s"}
+
+
 def cpu_baseline(workload: str) -> dict:
     sec, pts = oracle_step(workload)
-    return {"value": pts / sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"oracle (numpy/scipy fp64, dense current matrix) on {pts} points of "
-                      f"the same surface family and k, eps, leaf 64: tree + factor + solve + "
-                      f"adjoint in {sec:.1f} s"}
+    out = {"value": pts / sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+           "sample": f"oracle (numpy/scipy fp64, dense current matrix) on {pts} points of "
+                     f"the same surface family and k, eps, leaf 64: tree + factor + solve + "
+                     f"adjoint in {sec:.1f} s"}
+    one = single_core_oracle(workload)
+    if one is not None:
+        out["single_core"] = one
+    return out
 
 
 def run_reference(args, rank, world):
