@@ -12,6 +12,7 @@ Planted mistakes (a flipped double-layer sign, the target normal in place of
 the source normal, a dropped self term) are shown to fail these pins.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -85,6 +86,19 @@ def test_self_term_matches_disc_quadrature(w, k, eta):
     s_oracle = (diag - 0.5) / (-1j * eta)
     # two-term expansion: error of the next term, k^2 a^3 / 12
     assert abs(s_oracle - s_disc) <= 0.2 * k * k * a ** 3 + 1e-12
+
+
+def test_closed_form_eigenvalues_match_golden():
+    """The spherical-Bessel closed form used below agrees with the golden
+    values written out in elementary functions (tests/golden, two degrees,
+    two wavenumbers)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "sphere_cfie_eigenvalues.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 4
+    for n, k, eta, re_, im_ in rows:
+        want = complex(float(re_), float(im_))
+        assert abs(_lam(int(n), float(k), float(eta)) - want) <= 1e-12 * abs(want)
 
 
 @pytest.mark.parametrize("n_harm", [0, 1, 2])
