@@ -93,9 +93,9 @@ typedef struct fmmlu_opts {
                                  (no row distribution). Default 0.          */
   int schur_emulation;        /* products of the elimination (G1, G3, X_RR,
                                  W, Schur update) and of the root, and the
-                                 Gram matrix of the ID (inner dimension
-                                 >= 4 in mode 1, >= 32 in mode 2; smaller
-                                 ones run on fp64 FMA):
+                                 Gram matrix of the ID (every inner
+                                 dimension in mode 1; >= 32 in mode 2,
+                                 smaller ones on fp64 FMA):
                                  1 (default): tcgen05 tensor cores (TMEM
                                  accumulators) on an exact split of each
                                  complex128 operand into 7 bf16 digits; every
