@@ -251,18 +251,31 @@ int fmmlu_profile_reset(const fmmlu_handle* h);
  * must not pay the device-wide synchronisation of cudaFree.
  *   Work space: one fixed device array of FMMLU_NOALLOC_SCRATCH_BYTES (32 MiB)
  *   compiled into this library; every GPU that loads the library holds it
- *   until the process exits. A solve needs about 16 * nrhs * (N + 2 n0 + p)
- *   bytes (n0 from fmmlu_stats; p, the partial sums of one colour of the
- *   backward sweep, is at most a few times n0); larger requests return
+ *   until the process exits. A solve needs, each piece rounded up to 256 B,
+ *     16 nrhs N                  (the permuted right-hand sides)
+ *   + 2 x 16 nrhs n0             (the root's vectors)
+ *   + 16 nrhs 64 ceil(n0/128) + 4 nrhs   (the root's partial sums)
+ *   + 16 nrhs p                  (partial sums of the backward sweep)
+ *   + 4 (boxes nrhs + 1)         (counters)
+ *   bytes, where p is the largest sum over the boxes of one colour of
+ *   r x (column chunks + 1) and can reach tens of times n0 with small
+ *   chunks. fmmlu_stats reports the exact figure for nrhs = 1 as
+ *   "noalloc_bytes" ({"solve": ..., "adjoint": ...}); larger requests return
  *   FMMLU_ERR_LIMIT and change nothing.
  *   Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   before any stream capture. The address is kept for the life of the
+ *   process: after a cudaDeviceReset this entry point must not be used again.
+ *   Device: call it with the device current that was current at
+ *   fmmlu_factor (the one holding the factors); otherwise INVALID_ARG.
  *   Ordering: the call only enqueues work on `stream` and returns; synchronise
  *   the stream before reading x. All calls share the one array, which keeps
- *   the last call's contents (nothing in it needs to start at zero): calls on
- *   one stream are ordered, calls that overlap on the GPU (other streams or
- *   threads) race.
+ *   the last call's contents (nothing in it needs to start at zero: the
+ *   counters are cleared on the stream by every call): calls on one stream
+ *   are ordered, calls that overlap on the GPU (other streams or threads)
+ *   race.
+ *   Profiling: with opts.profile = 1 the launches are timed like those of
+ *   fmmlu_solve, the call waits for them, and fmmlu_stats counts them.
  *   b, x, nrhs as for fmmlu_solve. Errors: INVALID_ARG, LIMIT, CUDA. */
 int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, double* x, int nrhs,
                         int adjoint, void* stream);

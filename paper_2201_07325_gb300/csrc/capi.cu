@@ -146,6 +146,12 @@ struct UnitBuf {
 };
 
 constexpr int kRowChunkHost = 16;   // rows per CTA of the solve's R and S products
+// Real flops of one ID-matrix entry: comb_kernel_pair evaluates an entry and
+// its transpose partner from one distance in 51 adds and multiplies (the
+// coordinate differences, r^2, sqrt, 1/r^2, G, G (ikr - 1), both normal
+// projections, both combined-field values, the sqrt(w) scaling) plus one
+// sincos, which is not counted.
+constexpr double kKevalFlops = 25.5;
 
 inline uint64_t pkey(int x, int y) { return ((uint64_t)(uint32_t)x << 32) | (uint32_t)y; }
 
@@ -241,6 +247,7 @@ struct SolveCtx {
 
 struct fmmlu_handle {
   uint32_t magic = kHandleMagic;
+  int device = -1;             // CUDA device current at fmmlu_factor (holds the factors)
   int64_t n = 0;
   double k = 0, eta = 0, eps = 0;
   bool fp32 = false;
@@ -576,6 +583,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                  double k, double eps, const fmmlu_opts& opt, cudaStream_t st, fmmlu_handle* H) {
   const TreeHost& T = tree->T;
   const int64_t n = T.n;
+  CK(cudaGetDevice(&H->device));
   H->n = n;
   H->k = k;
   H->eta = std::isnan(opt.eta) ? k : opt.eta;
@@ -1148,7 +1156,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         const BoxRun& rr = run[e];
         double a = d.a, s_ = rr.s, r_ = rr.r, n_ = rr.n;
         double m = 2.0 * rr.nq + 2.0 * opt.n_proxy;
-        H->prof.add_work("assemble_id", 0, m * a * csz);
+        // one kernel evaluation per entry of M, kKevalFlops real flops each
+        // (besides the exponential); the outgoing and incoming rows of a pair
+        // share one distance and one exp(ikr)
+        H->prof.add_work("assemble_id", kKevalFlops * m * a, m * a * csz);
         if (gram_box[e]) {
           const double ns = H->fp32 ? 4.0 : 7.0, apad = std::ceil(a / 64.0) * 64.0;
           const double kt = std::ceil(m / 16.0) * 16.0;
@@ -1160,7 +1171,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           // products x 2 flops x m x a (a + 1) / 2
           const double pairs = H->fp32 ? 13.0 : 28.0;
           H->prof.add_work("gram", pairs * 8.0 * m * a * (a + 1) / 2.0,
-                           ns * 4.0 * apad * kt + 16.0 * a * a);
+                           ns * 4.0 * apad * kt + 16.0 * a * a, 8.0 * m * a * (a + 1) / 2.0);
           H->prof.add_work("pchol", pc, 16.0 * (a * a + a * s_ + s_ * r_));
         } else {
           double qr = 0;
@@ -1182,28 +1193,30 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           return ra * kk * (32.0 + 28.0) + rb * kk * (32.0 + 42.0);
         };
         H->prof.add_work(tc_s ? "gemm_g1_tc" : "gemm_g1", (tc_s ? c_tc : 8.0) * r_ * (a + n_) * s_,
-                         16.0 * (s_ * r_ + 2 * a * (a + n_)));
+                         16.0 * (s_ * r_ + 2 * a * (a + n_)), 8.0 * r_ * (a + n_) * s_);
         H->prof.add_work(tc_s ? "gemm_g3_tc" : "gemm_g3", (tc_s ? c_tc : 8.0) * (a + n_) * r_ * s_,
-                         16.0 * (s_ * r_ + 2 * a * (a + n_)));
+                         16.0 * (s_ * r_ + 2 * a * (a + n_)), 8.0 * (a + n_) * r_ * s_);
         const char* split_name = use_tc ? "tc_split" : "oz_split";
         if (tc_s) H->prof.add_work(split_name, 0, split(r_, a + n_, s_) + split(a + n_, r_, s_));
         H->prof.add_work(use_tc && tc_s ? "gemm_xrr_tc" : "gemm_xrr",
                          (use_tc && tc_s ? c_tc : 8.0) * r_ * r_ * s_,
-                         16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_));
+                         16.0 * (2 * r_ * r_ + r_ * s_ + s_ * r_), 8.0 * r_ * r_ * s_);
         if (use_tc && tc_s) H->prof.add_work(split_name, 0, split(r_, r_, s_));
         if (use_tc && ns_rmax >= kNsMin && rr.r >= kNsMin && rr.r <= ns_rmax) {
           // fp32 Gauss-Jordan, then two Newton-Schulz steps (two products each)
           H->prof.add_work("xrr_inverse32", 8.0 * r_ * r_ * r_, 16.0 * 3 * r_ * r_);
-          H->prof.add_work("ns_tc", 6.0 * c_tc * r_ * r_ * r_, 16.0 * 6 * 3 * r_ * r_);
+          H->prof.add_work("ns_tc", 6.0 * c_tc * r_ * r_ * r_, 16.0 * 6 * 3 * r_ * r_,
+                           6.0 * 8.0 * r_ * r_ * r_);
           H->prof.add_work(split_name, 0, 6.0 * split(r_, r_, r_));
         } else {
           H->prof.add_work("xrr_inverse", 8.0 * r_ * r_ * r_, 16.0 * 2 * r_ * r_);
         }
         H->prof.add_work(tc_r ? "gemm_w_tc" : "gemm_w", (tc_r ? c_tc : 8.0) * (s_ + n_) * r_ * r_,
-                         16.0 * (2 * (s_ + n_) * r_ + r_ * r_));
+                         16.0 * (2 * (s_ + n_) * r_ + r_ * r_), 8.0 * (s_ + n_) * r_ * r_);
         H->prof.add_work(tc_r ? "schur_tc" : "schur_update",
                          (tc_r ? c_tc : 8.0) * (s_ + n_) * (s_ + n_) * r_,
-                         16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)));
+                         16.0 * (2 * (s_ + n_) * r_ + 2 * (s_ + n_) * (s_ + n_)),
+                         8.0 * (s_ + n_) * (s_ + n_) * r_);
         if (tc_r) H->prof.add_work(split_name, 0, split(s_ + n_, r_, r_) + split(s_ + n_, s_ + n_, r_));
       }
     }
@@ -1322,9 +1335,9 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           const bool tcr = opt.schur_emulation == 1 && r_ >= kTcInnerMin;
           const double c = tcr ? 28.0 * 4.0 * 2.0 : 8.0;
           H->prof.add_work(tcr ? "root_w_tc" : "root_w", c * later * r_ * r_,
-                           16.0 * (2 * later * r_ + r_ * r_));
+                           16.0 * (2 * later * r_ + r_ * r_), 8.0 * later * r_ * r_);
           H->prof.add_work(tcr ? "root_schur_tc" : "root_schur", c * later * later * r_,
-                           16.0 * (2 * later * later + 2 * later * r_));
+                           16.0 * (2 * later * later + 2 * later * r_), 8.0 * later * later * r_);
         }
         rb += 1;
       }
@@ -1511,8 +1524,39 @@ int choose_chunk(const fmmlu_handle* H, int nrhs, bool adjoint, const double* b,
   return chunk;
 }
 
+// Algorithmic flops and bytes of one solve (both sweeps and the root) for the
+// per-kernel accounting of a profiled handle.
+void account_solve(const fmmlu_handle* H, const SolvePlan& plan, int nrhs) {
+  for (const auto& sg : plan.segs) {
+    H->prof.add_work("sweep_fwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
+    H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+    H->prof.add_work("sweep_bwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
+    H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+  }
+  const int n0 = H->n0;
+  for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
+    const double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
+    H->prof.add_work("root_fwd", 8.0 * nrhs * (r_ * r_ + later * r_),
+                     16.0 * (r_ * r_ + later * r_ + 2.0 * nrhs * (later + r_)));
+    H->prof.add_work("root_bwd", 8.0 * nrhs * (later * r_ + r_ * r_),
+                     16.0 * (later * r_ + r_ * r_ + nrhs * (later + 2.0 * r_)));
+  }
+}
+
+// The factors live on the device that was current at fmmlu_factor; a solve
+// must run with that device current.
+void check_device(const fmmlu_handle* H) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev != H->device)
+    throw Error(FMMLU_ERR_INVALID_ARG, "the current device (" + std::to_string(dev) +
+                                           ") is not the one the factors live on (" +
+                                           std::to_string(H->device) + ")");
+}
+
 void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, bool adjoint,
                 cudaStream_t st) {
+  check_device(H);
   std::lock_guard<std::mutex> lock(H->smu);
   const int chunk = choose_chunk(H, nrhs, adjoint, b, st);
   SolveCtx* c = get_ctx(H, nrhs, adjoint, st, chunk);
@@ -1536,21 +1580,42 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
   if (H->profile) {
     CK(cudaStreamSynchronize(st));
     H->prof.resolve();
-    for (const auto& sg : c->plan->segs) {
-      H->prof.add_work("sweep_fwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
-      H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
-      H->prof.add_work("sweep_bwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
-      H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
-    }
-    const int n0 = H->n0;
-    for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
-      const double r_ = std::min(H->nb_root, n0 - i0), later = n0 - i0 - r_;
-      H->prof.add_work("root_fwd", 8.0 * nrhs * (r_ * r_ + later * r_),
-                       16.0 * (r_ * r_ + later * r_ + 2.0 * nrhs * (later + r_)));
-      H->prof.add_work("root_bwd", 8.0 * nrhs * (later * r_ + r_ * r_),
-                       16.0 * (later * r_ + r_ * r_ + nrhs * (later + 2.0 * r_)));
-    }
+    account_solve(H, *c->plan, nrhs);
   }
+}
+
+inline size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Work-space layout of fmmlu_solve_noalloc for one (nrhs, direction): the
+// permuted vectors (16 nrhs N bytes), the root's two vectors (16 nrhs n0
+// each) and its partial sums, the backward sweep's partial sums (16 nrhs p,
+// p = part_max of the solve plan: the largest sum over one colour's boxes of
+// r x (column chunks + 1)) and one counter per eliminated box and right-hand
+// side; each piece starts on a 256-byte boundary. The plan is the one of an
+// earlier solve with this nrhs and direction (its tuned chunk size), else the
+// factorization's own: both exist already, nothing is built here.
+struct NoallocLayout {
+  std::shared_ptr<SolvePlan> plan;
+  size_t bv = 0, br = 0, bp = 0, bs = 0, bc = 0, need = 0;
+};
+
+NoallocLayout noalloc_layout(const fmmlu_handle* h, int nrhs, bool adj) {
+  NoallocLayout L;
+  {
+    std::lock_guard<std::mutex> lock(h->smu);
+    int chunk = h->chunk0;
+    auto it = h->chunk_for.find(std::make_pair(nrhs, adj ? 1 : 0));
+    if (it != h->chunk_for.end()) chunk = it->second;
+    auto pit = h->plans.find(chunk);
+    L.plan = pit != h->plans.end() ? pit->second : h->plans.at(h->chunk0);
+  }
+  L.bv = round256((size_t)16 * h->n * nrhs);
+  L.br = round256((size_t)16 * h->n0 * nrhs);
+  L.bp = round256(root_solve_scratch_bytes(h->n0, h->nb_root, nrhs));
+  L.bs = round256((size_t)16 * nrhs * L.plan->part_max);
+  L.bc = round256(counter_bytes(h, nrhs));
+  L.need = L.bv + 2 * L.br + L.bp + L.bs + L.bc;
+  return L;
 }
 
 }  // namespace
@@ -1697,6 +1762,8 @@ int fmmlu_stats(const fmmlu_handle* h, char* json, size_t cap) {
   if (!s.empty() && s.back() == '}') {
     s.pop_back();
     s += ", \"profile\": " + std::string(h->profile ? "true" : "false") +
+         ", \"noalloc_bytes\": {\"solve\": " + std::to_string(noalloc_layout(h, 1, false).need) +
+         ", \"adjoint\": " + std::to_string(noalloc_layout(h, 1, true).need) + "}" +
          ", \"kernels\": " + h->prof.json() + "}";
   }
   if (json && cap > 0) {
@@ -1793,8 +1860,6 @@ unsigned char* noalloc_scratch_for_current_device() {
   return g_noalloc_ptr[dev];
 }
 
-inline size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 }  // namespace
 
 extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, double* x, int nrhs,
@@ -1802,46 +1867,38 @@ extern "C" int fmmlu_solve_noalloc(const fmmlu_handle* h, const double* b, doubl
   return guard([&] {
     if (!h || h->magic != kHandleMagic || !b || !x || nrhs < 1)
       throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
+    check_device(h);
     cudaStream_t st = (cudaStream_t)stream;
     const bool adj = adjoint != 0;
-    std::shared_ptr<SolvePlan> plan;
-    {
-      // the plan of an earlier solve with this nrhs and direction, else the
-      // factorization's own (both exist already: nothing is built here)
-      std::lock_guard<std::mutex> lock(h->smu);
-      int chunk = h->chunk0;
-      auto it = h->chunk_for.find(std::make_pair(nrhs, adj ? 1 : 0));
-      if (it != h->chunk_for.end()) chunk = it->second;
-      auto pit = h->plans.find(chunk);
-      plan = pit != h->plans.end() ? pit->second : h->plans.at(h->chunk0);
-    }
-    const int64_t n = h->n;
-    const int n0 = h->n0;
-    const size_t bv = round256((size_t)16 * n * nrhs);
-    const size_t br = round256((size_t)16 * n0 * nrhs);
-    const size_t bp = round256(root_solve_scratch_bytes(n0, h->nb_root, nrhs));
-    const size_t bs = round256((size_t)16 * nrhs * plan->part_max);
-    const size_t bc = round256(counter_bytes(h, nrhs));
-    const size_t need = bv + 2 * br + bp + bs + bc;
-    if (need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
+    const NoallocLayout L = noalloc_layout(h, nrhs, adj);
+    if (L.need > (size_t)FMMLU_NOALLOC_SCRATCH_BYTES)
       throw Error(FMMLU_ERR_LIMIT,
-                  "fmmlu_solve_noalloc needs " + std::to_string(need) +
+                  "fmmlu_solve_noalloc needs " + std::to_string(L.need) +
                       " bytes of work space; the fixed array holds " +
                       std::to_string((size_t)FMMLU_NOALLOC_SCRATCH_BYTES));
     unsigned char* base = noalloc_scratch_for_current_device();
+    const int64_t n = h->n;
     SolveCtx c;   // views into the fixed array; owns nothing
     c.nrhs = nrhs;
     c.adjoint = adj;
-    c.plan = plan;
+    c.plan = L.plan;
     c.v = reinterpret_cast<double2*>(base);
-    c.vr = reinterpret_cast<double2*>(base + bv);
-    c.z = reinterpret_cast<double2*>(base + bv + br);
-    c.rscr = base + bv + 2 * br;
-    c.part = reinterpret_cast<double2*>(base + bv + 2 * br + bp);
-    c.cnt = reinterpret_cast<int*>(base + bv + 2 * br + bp + bs);
+    c.vr = reinterpret_cast<double2*>(base + L.bv);
+    c.z = reinterpret_cast<double2*>(base + L.bv + L.br);
+    c.rscr = base + L.bv + 2 * L.br;
+    c.part = reinterpret_cast<double2*>(base + L.bv + 2 * L.br + L.bp);
+    c.cnt = reinterpret_cast<int*>(base + L.bv + 2 * L.br + L.bp + L.bs);
+    // a profiled handle times these launches too and waits for them
+    ProfScope prof_scope(h->profile ? &h->prof : nullptr);
     launch_gather_vec(reinterpret_cast<const double2*>(b), h->d_perm, n, nrhs, c.v, st);
     run_sweeps(h, c, st);
     launch_scatter_vec(c.v, h->d_perm, n, nrhs, reinterpret_cast<double2*>(x), st);
     CK(cudaGetLastError());
+    if (h->profile) {
+      CK(cudaStreamSynchronize(st));
+      std::lock_guard<std::mutex> lock(h->smu);
+      h->prof.resolve();
+      account_solve(h, *L.plan, nrhs);
+    }
   });
 }

@@ -54,10 +54,11 @@ void Profiler::resolve() {
   pending.clear();
 }
 
-void Profiler::add_work(const char* name, double flops, double bytes) {
+void Profiler::add_work(const char* name, double flops, double bytes, double mflops) {
   ProfEntry& t = tot[name];
   t.flops += flops;
   t.bytes += bytes;
+  t.mflops += mflops < 0.0 ? flops : mflops;
 }
 
 void Profiler::reset() {
@@ -73,7 +74,8 @@ std::string Profiler::json() const {
   for (const auto& kv : tot) {
     o << (first ? "" : ", ") << "\"" << kv.first << "\": {\"launches\": " << kv.second.launches
       << ", \"ms\": " << kv.second.ms << ", \"flops\": " << kv.second.flops
-      << ", \"bytes\": " << kv.second.bytes << "}";
+      << ", \"bytes\": " << kv.second.bytes << ", \"method_flops\": " << kv.second.mflops
+      << "}";
     first = false;
   }
   o << "}";

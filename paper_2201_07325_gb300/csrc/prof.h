@@ -15,8 +15,12 @@ namespace fmmlu {
 struct ProfEntry {
   int64_t launches = 0;
   double ms = 0;      // summed CUDA-event durations
-  double flops = 0;   // algorithmic real flops attributed to these launches
+  double flops = 0;   // real flops the launches execute on their pipe (for the
+                      // exact-split tensor-core products: the bf16 digit-pair
+                      // flops)
   double bytes = 0;   // algorithmic DRAM bytes attributed to these launches
+  double mflops = 0;  // the method's own real flops (8 per complex multiply-add
+                      // of the fp64 product it computes, whatever the pipe)
 };
 
 struct Profiler {
@@ -29,7 +33,8 @@ struct Profiler {
   std::vector<cudaEvent_t> spare;
   cudaEvent_t get();
   void resolve();     // call after the stream has been synchronised
-  void add_work(const char* name, double flops, double bytes);
+  // mflops < 0: the method's flops equal the executed ones
+  void add_work(const char* name, double flops, double bytes, double mflops = -1.0);
   void reset();
   std::string json() const;
   ~Profiler();

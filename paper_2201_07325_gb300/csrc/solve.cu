@@ -13,6 +13,8 @@
 //   forward  z_i = D_i^{-1} b_i; b_later -= A[later, i] z_i
 //   backward x_i = z_i - D_i^{-1} A[i, later] x_later
 // (adjoint: the same with D_i^{-H}, A[i,later]^H, A[later,i]^H roles swapped).
+#include <mutex>
+
 #include "device_common.cuh"
 
 namespace fmmlu {
@@ -325,13 +327,19 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   if (t == 0) *ctr = 0;
 }
 
+// The dynamic shared-memory limit is a per-device attribute of each kernel:
+// set it once per device (thread-safe), with that device current.
+constexpr int kSmemAttrDevices = 64;
+static std::once_flag g_smem_attr_once[kSmemAttrDevices];
+
 static void set_smem_attr() {
-  static bool done = false;
-  if (done) return;
-  for (const void* f : {(const void*)k_sw_y, (const void*)k_sw_z, (const void*)k_sw_xr,
-                        (const void*)k_sw_xs, (const void*)k_fwd_c, (const void*)k_bwd_t})
-    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  done = true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSmemAttrDevices) return;
+  std::call_once(g_smem_attr_once[dev], [] {
+    for (const void* f : {(const void*)k_sw_y, (const void*)k_sw_z, (const void*)k_sw_xr,
+                          (const void*)k_sw_xs, (const void*)k_fwd_c, (const void*)k_bwd_t})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
 }
 
 void prepare_solve_kernels() { set_smem_attr(); }

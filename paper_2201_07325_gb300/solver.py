@@ -100,7 +100,7 @@ class FMMLUSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, b, fac: Factorization):
         ctx.fac = fac
-        return fac.solve(b)
+        return fac.solve(b).contiguous()
 
     @staticmethod
     def backward(ctx, grad_x):

@@ -49,12 +49,26 @@ def test_noalloc_solve_matches_allocating_solve():
                 torch.cuda.synchronize()
                 err = torch.linalg.vector_norm(x - want) / torch.linalg.vector_norm(want)
                 assert float(err) <= 1e-12
+        # the statistics state the work space one right-hand side needs
+        need = fac.stats()["noalloc_bytes"]
+        assert 16 * s.n < need["solve"] <= 32 * 1024 * 1024
+        assert 16 * s.n < need["adjoint"] <= 32 * 1024 * 1024
         # a request larger than the fixed array is refused and writes nothing
         big = 1 + (32 * 1024 * 1024) // (16 * s.n)
-        bb = torch.zeros((big, s.n), dtype=torch.complex128, device="cuda")
+        bb = torch.ones((big, s.n), dtype=torch.complex128, device="cuda")
         xx = torch.zeros_like(bb)
         rc = lib.fmmlu_solve_noalloc(fac.handle, ctypes.c_void_p(bb.data_ptr()),
                                      ctypes.c_void_p(xx.data_ptr()), big, 0, stream)
         assert rc == -8 and "fixed array" in pkg.fmmlu_last_error()
+        torch.cuda.synchronize()
+        assert int(torch.count_nonzero(xx)) == 0
+        # the shared array is still usable after the refusal
+        x = torch.full_like(b, complex(np.nan, np.nan))
+        rc = lib.fmmlu_solve_noalloc(fac.handle, ctypes.c_void_p(b.data_ptr()),
+                                     ctypes.c_void_p(x.data_ptr()), nrhs, 0, stream)
+        assert rc == 0, pkg.fmmlu_last_error()
+        torch.cuda.synchronize()
+        err = torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref)
+        assert float(err) <= 1e-12
     finally:
         fac.free()
