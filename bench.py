@@ -2,18 +2,25 @@
 """Benchmark of the FMM-LU hot path on one GB300 (or N replicas).
 
 One step = the whole hot path on one synthetic input, through the C ABI:
-fmmlu_build_tree + fmmlu_factor + fmmlu_solve + fmmlu_solve_adjoint on the
-50,000-point ellipsoid (semi-axes 1, 2, 0.5; k = 2 pi; eps = 1e-6; complex128,
-leaf 64, 300 proxy points). The metric is points per second of that step
-(the paper's S = n / t, for factor plus both solves), higher is better.
+fmmlu_build_tree + fmmlu_factor + fmmlu_solve + fmmlu_solve_adjoint of every
+right-hand side. Default workload: the 1,000,000-point ellipsoid (semi-axes
+1, 3, 0.5) with density graded 100:1 toward one tip, k = 20, eps = 1e-4, the
+mixed path (complex64 ID matrix, complex128 elimination and solves), 16
+plane-wave right-hand sides, leaf 64, 300 proxy points. The metric is points
+per second of that step (the paper's S = n / t, for the factor plus both
+batched solves), higher is better; the line also carries the factor seconds
+and solve milliseconds (t_factor_s, t_solve_ms) the metric names.
 
 Timing: W warm-up steps, then K steps, each preceded by an L2 flush (a 256 MiB
 write) outside its CUDA-event window; barrier + synchronize on both sides;
-max over ranks. Every kernel launch inside the timed steps is bracketed by
-CUDA events on its stream (opts.profile = 1) to obtain the dominant kernel's
-average launch duration for the roofline line. `e2e` repeats the step from
-pinned host buffers with the host-to-device copies of the inputs and the
-device-to-host copies of both solutions inside the timed region.
+max over ranks. The timed steps run without per-kernel events. One further
+step runs with CUDA events around every launch (opts.profile = 1): the
+per-kernel breakdown (top_kernels) and the dominant kernel's roofline come
+from it. `e2e` repeats the step K times from pinned host buffers with the
+host-to-device copies of the inputs and the device-to-host copies of both
+solutions inside the timed region. After the headline: the same workload on
+the plain fp64 path at the same eps (plain_fp64, mixed_vs_plain) and the
+other workloads (other_workloads), one warm-up and one timed step each.
 
 --impl reference times the CPU oracle (numpy/SciPy FP64) as it stands on this
 machine's host cores, each step a bounded sample of the same workload.
@@ -141,10 +148,16 @@ def measured_peaks() -> dict:
                 "bf16_sustained": (1700.0, "of fallback (1.7 PFLOP/s sustained)")}
 
 
-# translation unit (and its local headers) of each tensor-core kernel class
-_KERNEL_FILES = {name: ("tcgemm.cu", "device_common.cuh", "fmmlu_internal.h")
+# translation unit (and its local headers) of each kernel class whose DRAM
+# counters are recorded
+_COMMON = ("device_common.cuh", "fmmlu_internal.h")
+_KERNEL_FILES = {name: ("tcgemm.cu",) + _COMMON
                  for name in ("schur_tc", "gram", "gemm_g1_tc", "gemm_g3_tc", "gemm_w_tc",
                               "gemm_xrr_tc", "ns_tc", "root_w_tc", "root_schur_tc", "tc_split")}
+_KERNEL_FILES.update({"pchol": ("pchol.cu", "coop.cuh") + _COMMON,
+                      "xrr_inverse32": ("gj_dist.cu", "coop.cuh") + _COMMON,
+                      "assemble_id": ("assembly.cu",) + _COMMON,
+                      "assemble_elim": ("assembly.cu",) + _COMMON})
 
 
 def kernel_source_hash(kernel: str | None = None) -> str:
@@ -160,9 +173,12 @@ def kernel_source_hash(kernel: str | None = None) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
+def recorded_traffic(kernel: str, workload: str, alg_bytes_per_launch: float | None = None):
     """DRAM bytes per launch from the committed ncu summary, if it still
-    matches the current kernel sources (else None)."""
+    matches the current kernel sources (else None). A record taken on a
+    smaller case of the same surface family holds the ratio of DRAM bytes to
+    algorithmic bytes, applied here to this run's algorithmic bytes per
+    launch; an older record holds bytes per launch directly."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))
@@ -171,6 +187,8 @@ def recorded_traffic(kernel: str, workload: str):
     e = rec.get(workload, {}).get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
+    if "dram_per_alg_byte" in e:
+        return e["dram_per_alg_byte"] * alg_bytes_per_launch if alg_bytes_per_launch else None
     return e.get("dram_bytes_per_launch")
 
 
@@ -183,6 +201,156 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+_T0 = time.time()
+
+
+def log(msg: str):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    sys.stderr.write(f"[bench {time.time() - _T0:7.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
+def kernel_pipe(name: str, fp32_path: bool) -> str:
+    """Pipe that a kernel class's flops run on."""
+    if is_tensor_kernel(name):
+        return "tensor"
+    if name == "xrr_inverse32" or (fp32_path and name in ("cpqr", "assemble_id")):
+        return "fp32"
+    return "fp64"
+
+
+def kernel_roofline(name: str, e: dict, fp32_path: bool, peaks: dict, step_ms: float) -> dict:
+    """Roofline entry of one kernel class from a profiled step: the method's
+    own flops (8 real flops per complex multiply-add of the product it
+    computes; kernel evaluations for the ID assembly) per second against the
+    peak of the pipe the kernel runs on, or its algorithmic bytes per second
+    against HBM when it does no arithmetic of its own."""
+    sec = e["ms"] / 1e3
+    launches = max(1, e["launches"])
+    mfl = e.get("method_flops", e["flops"])
+    out = {"kernel": name, "launches": e["launches"], "avg_launch_ms": e["ms"] / launches,
+           "share_of_step": e["ms"] / max(1e-9, step_ms),
+           "alg_bytes_per_launch": e["bytes"] / launches,
+           "gbs": e["bytes"] / sec / 1e9 if sec > 0 else 0.0}
+    if sec <= 0:
+        return out
+    pipe = kernel_pipe(name, fp32_path)
+    if mfl > 0:
+        ach = mfl / sec / 1e12
+        if pipe == "tensor":
+            peak, src = peaks["bf16_sustained"]
+            out["pipe_achieved"] = e["flops"] / sec / 1e12
+            out["pipe_frac"] = out["pipe_achieved"] / peak
+            out["pipe_flops"] = "bf16 flops of the exact-split digit products"
+            bound = "tensor"
+        elif pipe == "fp32":
+            peak, src, bound = FP32_PEAK_TFLOPS, "fp32 lanes x 2 x max SM clock", "alu"
+        else:
+            peak, src, bound = FP64_PEAK_TFLOPS, "nominal fp64 of the profiling recipe", "alu"
+        out.update(bound=bound, achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   peak_source=src)
+    else:
+        gbs = e["bytes"] / sec / 1e9
+        peak, src = peaks["hbm"]
+        out.update(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak,
+                   peak_source=src)
+    return out
+
+
+class Workload:
+    """Device-resident inputs of one workload (right-hand sides as (nrhs, n))."""
+
+    def __init__(self, name: str, dev, n: int | None = None):
+        import torch
+        spec = synth.WORKLOADS[name]
+        self.name, self.k, self.eps = name, spec["k"], spec["eps"]
+        self.surf = synth.make_surface(name, n)
+        b = synth.make_rhs(name, self.surf)
+        self.b_np = np.ascontiguousarray(b.T) if b.ndim == 2 else b
+        self.nrhs = 1 if b.ndim == 1 else b.shape[1]
+        self.n = self.surf.n
+        self.pts = torch.from_numpy(self.surf.points).to(dev)
+        self.nrm = torch.from_numpy(self.surf.normals).to(dev)
+        self.wts = torch.from_numpy(self.surf.weights).to(dev)
+        self.b = torch.from_numpy(self.b_np).to(dev)
+        self.x = torch.empty_like(self.b)
+        self.y = torch.empty_like(self.b)
+
+
+def precision_code(pkg, name: str) -> int:
+    return {"fp64": pkg.PRECISION_FP64, "mixed": pkg.PRECISION_MIXED,
+            "auto": pkg.PRECISION_AUTO}[name]
+
+
+def gpu_step(pkg, w: Workload, opts, st, evs=None):
+    """One pass of the hot path: tree, factor, solve and adjoint solve of all
+    right-hand sides. Returns the handle (the caller frees it)."""
+    if evs:
+        evs[0].record(st)
+    t = pkg.fmmlu_build_tree(w.pts, opts)
+    if evs:
+        evs[1].record(st)
+    h = pkg.fmmlu_factor(t, w.pts, w.nrm, w.wts, w.k, w.eps, opts)
+    pkg.fmmlu_free(t)
+    if evs:
+        evs[2].record(st)
+    pkg.fmmlu_solve(h, w.b, w.x, w.n)
+    if evs:
+        evs[3].record(st)
+    pkg.fmmlu_solve_adjoint(h, w.b, w.y, w.n)
+    if evs:
+        evs[4].record(st)
+    return h
+
+
+def timed_steps(pkg, w: Workload, opts, st, steps: int, flush, barrier=lambda: None):
+    """Time `steps` passes with CUDA events (L2 flushed before each, outside
+    the events). Returns (mean ms per step, mean component ms [tree, factor,
+    solve, adjoint], stats of the last handle)."""
+    import torch
+    comp = np.zeros(4)
+    total = 0.0
+    stats = None
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        h = gpu_step(pkg, w, opts, st, evs)
+        torch.cuda.synchronize()
+        barrier()
+        comp += np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(4)])
+        total += evs[0].elapsed_time(evs[4])
+        stats = pkg.fmmlu_stats(h)
+        pkg.fmmlu_free(h)
+    return total / steps, comp / steps, stats
+
+
+def arm_summary(w: Workload, precision: str, step_ms: float, comp, stats) -> dict:
+    return {"workload": w.name, "n": w.n, "k": w.k, "eps": w.eps, "nrhs": w.nrhs,
+            "precision": stats["precision"], "requested": precision,
+            "points_per_s": w.n / (step_ms / 1e3), "ms_per_step": step_ms,
+            "t_tree_ms": comp[0], "t_factor_s": comp[1] / 1e3, "t_solve_ms": comp[2],
+            "t_adjoint_ms": comp[3], "n0": stats["n0"], "factor_bytes": stats["factor_bytes"]}
+
+
+def dense_residual(pkg, w: Workload) -> float:
+    """||A x - b|| / ||b|| of the first solution by the dense on-the-fly GPU
+    product (O(N^2): used up to a few hundred thousand points)."""
+    import torch
+    x0 = w.x[0].clone() if w.x.dim() == 2 else w.x.clone()
+    b0 = w.b[0] if w.b.dim() == 2 else w.b
+    y = torch.empty_like(x0)
+    pkg.fmmlu_matvec(w.pts, w.nrm, w.wts, w.k, w.k, x0, y)
+    return float(torch.linalg.vector_norm(y - b0) / torch.linalg.vector_norm(b0))
+
+
+# other workloads measured beside the headline (one warm-up step that also
+# tunes, then one timed step each)
+EXTRA_ARMS = [("ellipsoid50k", "fp64"), ("torus200k", "mixed"), ("torus200k", "fp64"),
+              ("sphere100k", "fp64")]
 
 
 def run_gpu(args, rank, world):
@@ -201,208 +369,169 @@ def run_gpu(args, rank, world):
         if dist is not None:
             dist.barrier()
 
-    spec = synth.WORKLOADS[args.workload]
-    k, eps = spec["k"], spec["eps"]
-    surf = synth.make_surface(args.workload)
-    b_np = synth.make_rhs(args.workload, surf)
-    if b_np.ndim == 2:
-        b_np = np.ascontiguousarray(b_np.T)          # (nrhs, n)
-    nrhs = 1 if b_np.ndim == 1 else b_np.shape[0]
-    n = surf.n
     pkg.load_library()
-    precision = {"fp64": pkg.PRECISION_FP64, "mixed": pkg.PRECISION_MIXED,
-                 "auto": pkg.PRECISION_AUTO}[args.precision]
-    opts = pkg.fmmlu_default_opts(leaf_size=64, precision=precision, profile=1)
-    pts = torch.from_numpy(surf.points).to(dev)
-    nrm = torch.from_numpy(surf.normals).to(dev)
-    wts = torch.from_numpy(surf.weights).to(dev)
-    b = torch.from_numpy(b_np).to(dev)
-    x = torch.empty_like(b)
-    y = torch.empty_like(b)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    log(f"inputs {args.workload}")
+    w = Workload(args.workload, dev)
+    n, nrhs, k, eps = w.n, w.nrhs, w.k, w.eps
+    log("warm-up")
+    precision = precision_code(pkg, args.precision)
+    opts = pkg.fmmlu_default_opts(leaf_size=64, precision=precision)
 
-    def one_step(handles, evs=None):
-        if evs:
-            evs[0].record(st)
-        t = pkg.fmmlu_build_tree(pts, opts)
-        if evs:
-            evs[1].record(st)
-        h = pkg.fmmlu_factor(t, pts, nrm, wts, k, eps, opts)
-        pkg.fmmlu_free(t)
-        if evs:
-            evs[2].record(st)
-        pkg.fmmlu_solve(h, b, x, n)
-        if evs:
-            evs[3].record(st)
-        pkg.fmmlu_solve_adjoint(h, b, y, n)
-        if evs:
-            evs[4].record(st)
-        handles.append(h)
-
+    # ---- headline: W warm-up steps, K timed steps (no per-kernel events) ----
     for _ in range(args.warmup):
-        hs = []
-        one_step(hs)
-        for h in hs:
-            pkg.fmmlu_free(h)
+        pkg.fmmlu_free(gpu_step(pkg, w, opts, st))
     torch.cuda.synchronize()
-
+    log("timed steps")
     sampler = ClockSampler(local)
     sampler.start()
-    comp = np.zeros(4)
-    total_ms = 0.0
     launches0 = pkg.fmmlu_kernel_launches()
-    kern = {}
-    last_stats = None
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        barrier()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        hs = []
-        one_step(hs, evs)
-        torch.cuda.synchronize()
-        barrier()
-        ts = [evs[i].elapsed_time(evs[i + 1]) for i in range(4)]
-        comp += np.array(ts)
-        total_ms += evs[0].elapsed_time(evs[4])
-        last_stats = pkg.fmmlu_stats(hs[0])
-        for name, e in last_stats["kernels"].items():
-            acc = kern.setdefault(name, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
-            for f in acc:
-                acc[f] += e[f]
-        keep_x = x.clone()
-        for h in hs:
-            pkg.fmmlu_free(h)
+    mean_ms, comp, stats = timed_steps(pkg, w, opts, st, args.steps, flush, barrier)
     launches = pkg.fmmlu_kernel_launches() - launches0
     clocks = sampler.stop()
-    step_ms = max_over_ranks(total_ms / args.steps, dist, dev)
+    step_ms = max_over_ranks(mean_ms, dist, dev)
     value = n * world / (step_ms / 1e3)
+    fp32_path = stats["precision"] == "mixed"
 
-    # residual of the last solution (dense on-the-fly product, outside timing)
-    yv = torch.empty_like(keep_x)
-    pkg.fmmlu_matvec(pts, nrm, wts, k, k, keep_x, yv)
-    residual = float(torch.linalg.vector_norm(yv - b) / torch.linalg.vector_norm(b))
+    log(f"timed: {step_ms:.1f} ms per step; profiled step")
+    # ---- per-kernel breakdown: one more step with CUDA events on every launch
+    opts_prof = pkg.fmmlu_default_opts(leaf_size=64, precision=precision, profile=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record(st)
+    h = gpu_step(pkg, w, opts_prof, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    prof_step_ms = e0.elapsed_time(e1)
+    kern = pkg.fmmlu_stats(h)["kernels"]
+    pkg.fmmlu_free(h)
+    peaks = measured_peaks()
+    roofs = {nm: kernel_roofline(nm, e, fp32_path, peaks, prof_step_ms) for nm, e in kern.items()
+             if e["ms"] > 0}
+    order = sorted(roofs, key=lambda nm: -roofs[nm]["avg_launch_ms"] * roofs[nm]["launches"])
+    dname = order[0]
+    roof = dict(roofs[dname])
+    for rk, nm in enumerate(order[:3]):
+        roofs[nm]["traffic"] = recorded_traffic(nm, args.workload, roofs[nm]["alg_bytes_per_launch"])
+    roof["traffic"] = roofs[dname]["traffic"]
+    roof["measured_in"] = ("a profiled step after the timed steps (CUDA events around every "
+                           "launch on its stream); share_of_step is of that step")
+    roof["flops_counted"] = ("the method's: 8 real flops per complex multiply-add of the "
+                             "product computed (pipe_achieved counts the bf16 digit-pair flops)")
 
-    # repeated solves with one factorization (the serving case): after the
-    # first solve of each direction the sweeps replay as one CUDA graph
-    opts_rep = pkg.fmmlu_default_opts(leaf_size=64, precision=precision)
-    t = pkg.fmmlu_build_tree(pts, opts_rep)
-    h = pkg.fmmlu_factor(t, pts, nrm, wts, k, eps, opts_rep)
-    pkg.fmmlu_free(t)
+    log("repeated solves")
+    # ---- repeated solves with one factorization (graph replay) -------------
+    h = gpu_step(pkg, w, opts, st)
     rep = {}
     for name, fn in (("solve", pkg.fmmlu_solve), ("adjoint", pkg.fmmlu_solve_adjoint)):
         for _ in range(3):
-            fn(h, b, x, n)
+            fn(h, w.b, w.x, n)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        reps = 10
         e0.record(st)
+        reps = 10
         for _ in range(reps):
-            fn(h, b, x, n)
+            fn(h, w.b, w.x, n)
         e1.record(st)
         torch.cuda.synchronize()
         rep[name] = e0.elapsed_time(e1) / reps
     pkg.fmmlu_free(h)
 
-    # end to end from pinned host buffers
-    hp = [torch.from_numpy(a).pin_memory() for a in (surf.points, surf.normals, surf.weights)]
-    hb = torch.from_numpy(b_np).pin_memory()
+    log("end to end")
+    # ---- end to end from pinned host buffers, K steps ------------------------
+    hp = [torch.from_numpy(a).pin_memory() for a in (w.surf.points, w.surf.normals,
+                                                      w.surf.weights)]
+    hb = torch.from_numpy(w.b_np).pin_memory()
     hx = torch.empty_like(hb).pin_memory()
     hy = torch.empty_like(hb).pin_memory()
     e2e_ms = 0.0
-    opts_np = pkg.fmmlu_default_opts(leaf_size=64, precision=precision)
-    e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
         dp, dn, dw = (a.to(dev, non_blocking=True) for a in hp)
         db = hb.to(dev, non_blocking=True)
         dx = torch.empty_like(db)
         dy = torch.empty_like(db)
-        t = pkg.fmmlu_build_tree(dp, opts_np)
-        h = pkg.fmmlu_factor(t, dp, dn, dw, k, eps, opts_np)
+        t = pkg.fmmlu_build_tree(dp, opts)
+        hh = pkg.fmmlu_factor(t, dp, dn, dw, k, eps, opts)
         pkg.fmmlu_free(t)
-        pkg.fmmlu_solve(h, db, dx, n)
-        pkg.fmmlu_solve_adjoint(h, db, dy, n)
+        pkg.fmmlu_solve(hh, db, dx, n)
+        pkg.fmmlu_solve_adjoint(hh, db, dy, n)
         hx.copy_(dx, non_blocking=True)
         hy.copy_(dy, non_blocking=True)
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
         e2e_ms += e0.elapsed_time(e1)
-        pkg.fmmlu_free(h)
-    e2e_ms = max_over_ranks(e2e_ms / e2e_steps, dist, dev)
+        pkg.fmmlu_free(hh)
+        del dp, dn, dw, db, dx, dy
+    e2e_ms = max_over_ranks(e2e_ms / args.steps, dist, dev)
     h2d = sum(a.numel() * a.element_size() for a in hp) + hb.numel() * hb.element_size()
     d2h = 2 * hb.numel() * hb.element_size()
+    del hp, hb, hx, hy
 
-    # roofline of the dominant kernel over the timed region
-    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
-    fp32_path = precision == pkg.PRECISION_MIXED or (precision == pkg.PRECISION_AUTO
-                                                     and eps >= 1e-5)
-    fp32_kernels = ({"cpqr", "assemble_id"} if fp32_path else set()) | {"xrr_inverse32"}
-    peaks = measured_peaks()
-    if is_tensor_kernel(dname):
-        # exact-split products on the bf16 tensor cores: the bf16 flops of the
-        # digit-pair products against the measured sustained bf16 rate
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        peak, src = peaks["bf16_sustained"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": dname, "peak_source": src}
-    elif d["flops"] > 0:
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        peak = FP32_PEAK_TFLOPS if dname in fp32_kernels else FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": dname,
-                "peak_source": "fp32 FFMA units x clock" if dname in fp32_kernels
-                else "nominal fp64 of the profiling recipe (1.25 TFLOP/s)"}
-    else:
-        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        peak, src = peaks["hbm"]
-        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                "frac": gbs / peak, "kernel": dname, "peak_source": src}
-    tr = recorded_traffic(dname, args.workload)
-    roof["traffic"] = tr
-    roof["avg_launch_ms"] = d["ms"] / max(1, d["launches"])
-    roof["launches"] = d["launches"]
-    roof["share_of_step"] = d["ms"] / max(1e-9, total_ms)
-    top = sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:8]
-
+    headline = arm_summary(w, args.precision, step_ms, comp, stats)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if not fp32_path else "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if fp32_path else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "k": k, "eps": eps,
-                   "precision": args.precision, "nrhs": nrhs, "leaf_size": 64,
-                   "n_proxy": 300, "l2": "flushed between steps (256 MiB write)",
+                   "precision": stats["precision"], "nrhs": nrhs, "leaf_size": 64,
+                   "n_proxy": 300, "step": "tree + factor + solve + adjoint solve of all "
+                                           "right-hand sides",
+                   "l2": "flushed between steps (256 MiB write); the factor's working set "
+                         "is far larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "t_tree_ms": comp[0] / args.steps, "t_factor_s": comp[1] / args.steps / 1e3,
-        "t_solve_ms": comp[2] / args.steps, "t_adjoint_ms": comp[3] / args.steps,
-        "t_solve_repeat_ms": rep["solve"], "t_adjoint_repeat_ms": rep["adjoint"],
-        "n0": last_stats["n0"], "factor_bytes": last_stats["factor_bytes"],
-        "residual": residual,
+        "t_tree_ms": comp[0], "t_factor_s": comp[1] / 1e3, "t_solve_ms": comp[2],
+        "t_adjoint_ms": comp[3], "t_solve_repeat_ms": rep["solve"],
+        "t_adjoint_repeat_ms": rep["adjoint"], "n0": stats["n0"],
+        "factor_bytes": stats["factor_bytes"],
         "e2e": {"value": n * world / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms, "steps": args.steps},
         "gpu_launches": launches,
+        "gpu_launches_per_step": launches / max(1, args.steps),
         "roofline": roof,
-        "top_kernels": {nm: {"ms_per_step": e["ms"] / args.steps,
-                             "launches_per_step": e["launches"] / args.steps,
-                             "tflops": (e["flops"] / (e["ms"] / 1e3) / 1e12) if e["ms"] else 0,
-                             "unit": "bf16 TFLOP/s" if is_tensor_kernel(nm) else
-                                     ("TFLOP/s" if e["flops"] else "GB/s"),
-                             "gbs": (e["bytes"] / (e["ms"] / 1e3) / 1e9) if e["ms"] else 0}
-                        for nm, e in top},
+        "top_kernels": {nm: roofs[nm] for nm in order[:10]},
         "clocks": clocks,
     }
+    # ---- plain fp64 at the same eps, and the other workloads ---------------
+    if not args.no_extra and world == 1:
+        arms = []
+        if stats["precision"] != "fp64":
+            arms.append((args.workload, "fp64"))
+        arms += [a for a in EXTRA_ARMS if a[0] != args.workload]
+        extra = {}
+        for wl, prec in arms:
+            log(f"arm {wl} {prec}")
+            wa = w if wl == args.workload else Workload(wl, dev)
+            oa = pkg.fmmlu_default_opts(leaf_size=64, precision=precision_code(pkg, prec))
+            pkg.fmmlu_free(gpu_step(pkg, wa, oa, st))
+            ms, cp, sa = timed_steps(pkg, wa, oa, st, 1, flush)
+            row = arm_summary(wa, prec, ms, cp, sa)
+            if wa.n <= 200000:
+                row["residual"] = dense_residual(pkg, wa)
+            extra[f"{wl}_{prec}"] = row
+            del wa
+            torch.cuda.empty_cache()
+        log("arms done")
+        plain = extra.pop(f"{args.workload}_fp64", None)
+        if plain is not None:
+            out["plain_fp64"] = plain
+            out["mixed_vs_plain"] = {
+                "factor_speedup": plain["t_factor_s"] / headline["t_factor_s"],
+                "step_speedup": plain["ms_per_step"] / headline["ms_per_step"],
+                "factor_bytes_ratio": headline["factor_bytes"] / plain["factor_bytes"]}
+        out["other_workloads"] = extra
+    del w
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload)
+        log("cpu baseline")
+        out["cpu_baseline"] = cpu_baseline(args.workload, pkg, dev, opts)
     if dist is not None:
         dist.destroy_process_group()
     return out
@@ -412,18 +541,18 @@ def run_gpu(args, rank, world):
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-SAMPLE_N = 2500
+BASELINE_SIZES = (2000, 4000)
+REFERENCE_N = 1200
 
 
-def oracle_step(workload: str, nsample: int = SAMPLE_N):
+def oracle_step(workload: str, nsample: int):
     """The oracle on a bounded sample of the workload: same surface family,
-    k, eps, leaf size; N = nsample. Returns (seconds, points)."""
+    k, eps, leaf size and right-hand sides, N = nsample; tree + factor +
+    solve + adjoint solve. Returns (seconds, points)."""
     from oracle import rss
     spec = synth.WORKLOADS[workload]
     surf = synth.make_surface(workload, nsample)
     b = synth.make_rhs(workload, surf)
-    if b.ndim == 2:
-        b = b[:, 0]
     t0 = time.perf_counter()
     F = rss.factor(surf.points, surf.normals, surf.weights, spec["k"], spec["eps"],
                    leaf_size=64)
@@ -432,7 +561,7 @@ def oracle_step(workload: str, nsample: int = SAMPLE_N):
     return time.perf_counter() - t0, nsample
 
 
-def single_core_oracle(workload: str, nsample: int = SAMPLE_N):
+def single_core_oracle(workload: str, nsample: int):
     """The oracle step in a child process limited to one thread (the paper's
     single-core setting); None when the child fails."""
     env = dict(os.environ)
@@ -443,21 +572,39 @@ def single_core_oracle(workload: str, nsample: int = SAMPLE_N):
             % (workload, nsample))
     try:
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
-                           text=True, timeout=300)
+                           text=True, timeout=600)
         sec, pts = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception:
         return None
-    return {"value": pts / sec, "unit": UNIT, "cores": 1,
+    return {"value": pts / sec, "unit": UNIT, "cores": 1, "n": pts, "seconds": sec,
             "sample": f"oracle on {pts} points, one thread: {sec:.1f} s"}
 
 
-def cpu_baseline(workload: str) -> dict:
-    sec, pts = oracle_step(workload)
-    out = {"value": pts / sec, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-           "sample": f"oracle (numpy/scipy fp64, dense current matrix) on {pts} points of "
-                     f"the same surface family and k, eps, leaf 64: tree + factor + solve + "
-                     f"adjoint in {sec:.1f} s"}
-    one = single_core_oracle(workload)
+def cpu_baseline(workload: str, pkg=None, dev=None, opts=None) -> dict:
+    """The oracle (as it stands) on samples of the workload's surface family,
+    all host cores, with the GPU's step time at the same sizes beside it."""
+    per_n = []
+    for nn in BASELINE_SIZES:
+        sec, pts = oracle_step(workload, nn)
+        row = {"n": pts, "oracle_s": sec, "oracle_points_per_s": pts / sec}
+        if pkg is not None:
+            import torch
+            wsm = Workload(workload, dev, nn)
+            pkg.fmmlu_free(gpu_step(pkg, wsm, opts, torch.cuda.current_stream()))
+            flush = torch.empty(1, device=dev)
+            ms, _, _ = timed_steps(pkg, wsm, opts, torch.cuda.current_stream(), 3, flush)
+            row["gpu_s"] = ms / 1e3
+            row["gpu_over_oracle"] = sec / (ms / 1e3)
+        per_n.append(row)
+    last = per_n[-1]
+    out = {"value": last["oracle_points_per_s"], "unit": UNIT, "cores": cpu_cores(),
+           "kind": "oracle", "per_n": per_n,
+           "sample": f"oracle (numpy/scipy fp64, dense current matrix) on {last['n']} points "
+                     f"of the same surface family, k, eps, leaf 64 and right-hand sides: tree + "
+                     f"factor + solve + adjoint in {last['oracle_s']:.1f} s (value); also "
+                     f"{', '.join(str(r['n']) for r in per_n[:-1])} points (per_n, with the "
+                     f"GPU's time at each size)"}
+    one = single_core_oracle(workload, BASELINE_SIZES[0])
     if one is not None:
         out["single_core"] = one
     return out
@@ -467,10 +614,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     for _ in range(args.warmup):
-        oracle_step(args.workload, 1200)
+        oracle_step(args.workload, REFERENCE_N)
     tot, pts = 0.0, 0
     for _ in range(args.steps):
-        s, p = oracle_step(args.workload, 1200)
+        s, p = oracle_step(args.workload, REFERENCE_N)
         tot += s
         pts += p
     value = pts / tot
@@ -478,12 +625,12 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample_n": 1200,
+            "config": {"workload": args.workload, "sample_n": REFERENCE_N,
                        "note": "CPU oracle on a bounded sample of the workload"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
                              "kind": "oracle",
-                             "sample": "oracle on 1200 points of the same surface family, "
-                                       "k, eps, leaf 64 per step"},
+                             "sample": f"oracle on {REFERENCE_N} points of the same surface "
+                                       f"family, k, eps, leaf 64 and right-hand sides per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -580,9 +727,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ellipsoid50k", choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "auto"])
+    ap.add_argument("--workload", default="ellipsoid1m", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="auto", choices=["fp64", "mixed", "auto"],
+                    help="auto: mixed when eps >= 1e-5 (the 1M-point workload: eps = 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the plain-fp64 arm and the other workloads")
     ap.add_argument("--factor-once", action="store_true",
                     help="one profiled tree + factor of the workload (ncu captures); "
                          "prints the per-kernel algorithmic flops/bytes")

@@ -41,7 +41,7 @@ def test_recorded_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
 def test_unlisted_kernels_hash_all_sources(tmp_path, monkeypatch):
     csrc = _fake_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    h = bench.kernel_source_hash("pchol")
+    h = bench.kernel_source_hash("sweep_fwd")
     assert h == bench.kernel_source_hash()
     (csrc / "solve.cu").write_text("// changed\n")
-    assert bench.kernel_source_hash("pchol") != h
+    assert bench.kernel_source_hash("sweep_fwd") != h
