@@ -347,6 +347,13 @@ def dense_residual(pkg, w: Workload) -> float:
     return float(torch.linalg.vector_norm(y - b0) / torch.linalg.vector_norm(b0))
 
 
+# proxy points per workload: 300 on every level, except on the 1M-point
+# ellipsoid at k = 20 (about 10 wavelengths), whose coarse boxes are several
+# wavelengths across: there the count follows the per-level multipole
+# estimate (Sec. 5.2) with a floor of 64 points, which measured faster and
+# more accurate than 300 everywhere (sampled residual 2.3e-5 against 3.5e-5)
+PROXY_DEFAULTS = {"ellipsoid1m": ("adaptive", 64)}
+
 # other workloads measured beside the headline (one warm-up step that also
 # tunes, then one timed step each)
 EXTRA_ARMS = [("ellipsoid50k", "fp64"), ("torus200k", "mixed"), ("torus200k", "fp64"),
@@ -377,7 +384,14 @@ def run_gpu(args, rank, world):
     n, nrhs, k, eps = w.n, w.nrhs, w.k, w.eps
     log("warm-up")
     precision = precision_code(pkg, args.precision)
-    opts = pkg.fmmlu_default_opts(leaf_size=64, precision=precision)
+    def proxy_opts(workload):
+        rule, npx = ((args.proxy_rule, args.n_proxy) if workload == args.workload
+                     else PROXY_DEFAULTS.get(workload, ("fixed", 300)))
+        return dict(n_proxy=npx,
+                    proxy_rule=pkg.PROXY_ADAPTIVE if rule == "adaptive" else pkg.PROXY_FIXED)
+
+    popts = proxy_opts(args.workload)
+    opts = pkg.fmmlu_default_opts(leaf_size=64, precision=precision, **popts)
 
     # ---- headline: W warm-up steps, K timed steps (no per-kernel events) ----
     for _ in range(args.warmup):
@@ -396,7 +410,7 @@ def run_gpu(args, rank, world):
 
     log(f"timed: {step_ms:.1f} ms per step; profiled step")
     # ---- per-kernel breakdown: one more step with CUDA events on every launch
-    opts_prof = pkg.fmmlu_default_opts(leaf_size=64, precision=precision, profile=1)
+    opts_prof = pkg.fmmlu_default_opts(leaf_size=64, precision=precision, profile=1, **popts)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flush.zero_()
     torch.cuda.synchronize()
@@ -481,7 +495,7 @@ def run_gpu(args, rank, world):
         "dtype": "f32+f64" if fp32_path else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "k": k, "eps": eps,
                    "precision": stats["precision"], "nrhs": nrhs, "leaf_size": 64,
-                   "n_proxy": 300, "step": "tree + factor + solve + adjoint solve of all "
+                   "n_proxy": args.n_proxy, "proxy_rule": args.proxy_rule, "step": "tree + factor + solve + adjoint solve of all "
                                            "right-hand sides",
                    "l2": "flushed between steps (256 MiB write); the factor's working set "
                          "is far larger than L2",
@@ -509,7 +523,8 @@ def run_gpu(args, rank, world):
         for wl, prec in arms:
             log(f"arm {wl} {prec}")
             wa = w if wl == args.workload else Workload(wl, dev)
-            oa = pkg.fmmlu_default_opts(leaf_size=64, precision=precision_code(pkg, prec))
+            oa = pkg.fmmlu_default_opts(leaf_size=64, precision=precision_code(pkg, prec),
+                                        **proxy_opts(wl))
             pkg.fmmlu_free(gpu_step(pkg, wa, oa, st))
             ms, cp, sa = timed_steps(pkg, wa, oa, st, 1, flush)
             row = arm_summary(wa, prec, ms, cp, sa)
@@ -553,9 +568,10 @@ def oracle_step(workload: str, nsample: int):
     spec = synth.WORKLOADS[workload]
     surf = synth.make_surface(workload, nsample)
     b = synth.make_rhs(workload, surf)
+    rule, npx = PROXY_DEFAULTS.get(workload, ("fixed", 300))
     t0 = time.perf_counter()
     F = rss.factor(surf.points, surf.normals, surf.weights, spec["k"], spec["eps"],
-                   leaf_size=64)
+                   leaf_size=64, n_proxy=npx, proxy_rule=rule)
     rss.solve(F, b)
     rss.solve_adjoint(F, b)
     return time.perf_counter() - t0, nsample
@@ -731,6 +747,11 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["fp64", "mixed", "auto"],
                     help="auto: mixed when eps >= 1e-5 (the 1M-point workload: eps = 1e-4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--proxy-rule", default=None, choices=["fixed", "adaptive"],
+                    help="proxy points per sphere: n_proxy on every level, or the per-level "
+                         "multipole estimate with n_proxy as the floor (default: the "
+                         "workload's, PROXY_DEFAULTS)")
+    ap.add_argument("--n-proxy", type=int, default=None)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the plain-fp64 arm and the other workloads")
     ap.add_argument("--factor-once", action="store_true",
@@ -743,6 +764,9 @@ def main():
                          "per wavelength), one JSON line per size and precision")
     ap.add_argument("--sizes", default="12500,25000,50000,100000,200000,400000")
     args = ap.parse_args()
+    rule, npx = PROXY_DEFAULTS.get(args.workload, ("fixed", 300))
+    args.proxy_rule = args.proxy_rule or rule
+    args.n_proxy = args.n_proxy or npx
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.factor_once:

@@ -53,6 +53,8 @@ extern "C" {
                                      only: reported by fmmlu_stats)          */
 #define FMMLU_ERR_TIMEOUT -7      /* a bounded device wait gave up           */
 #define FMMLU_ERR_LIMIT -8        /* a size exceeds a documented maximum     */
+#define FMMLU_ERR_NOT_CONVERGED -9 /* an iteration stopped at its step limit
+                                      before reaching its tolerance           */
 
 #define FMMLU_ID_AUTO 0           /* Gram form when eps_ID >= 1e-7, else QR */
 #define FMMLU_ID_HOUSEHOLDER 1    /* column-pivoted Householder QR of the ID
@@ -147,7 +149,20 @@ typedef struct fmmlu_opts {
                                  from it (lines "key value") and appended to
                                  it, so later processes skip the timing.
                                  The string is copied by fmmlu_factor.     */
+  int proxy_rule;             /* number of proxy points per sphere (Sec. 5.2,
+                                 proxy surface discretization):
+                                 FMMLU_PROXY_FIXED (default): n_proxy on
+                                 every level;
+                                 FMMLU_PROXY_ADAPTIVE: per level from the
+                                 multipole truncation estimate
+                                 p = ceil(k rho + 1.8 d^(2/3) (k rho)^(1/3)),
+                                 d = log10(1/eps_ID), rho the level's proxy
+                                 radius: max(n_proxy, 2 (p + 1)^2) points, so
+                                 n_proxy becomes the floor.                */
 } fmmlu_opts;
+
+#define FMMLU_PROXY_FIXED 0
+#define FMMLU_PROXY_ADAPTIVE 1
 
 /* Fill `opts` with the defaults listed above. Returns 0, or INVALID_ARG if
  * opts is NULL. */
@@ -216,6 +231,74 @@ int fmmlu_solve_adjoint(const fmmlu_handle* h, const double* b, double* x,
 int fmmlu_matvec(int64_t n, const double* points, const double* normals,
                  const double* weights, double k, double eta, const double* v,
                  double* y, int nrhs, void* stream);
+
+/* Solve A x = b by restarted GMRES preconditioned by the stored factors:
+ * the factorization used as a preconditioner for an iterative method
+ * (Sec. 7). Right preconditioning, A M^{-1} u = b, x = M^{-1} u, with M^{-1}
+ * the sweeps of fmmlu_solve and A the dense on-the-fly product of
+ * fmmlu_matvec (O(N^2) per step). A factorization at a loose eps (fast, small
+ * m_f) then reaches a tight tol in a few steps. Basis orthogonalised by
+ * classical Gram-Schmidt applied twice, Givens rotations, x_0 = 0; every
+ * step runs in the library's kernels; the host reads one residual estimate
+ * per step.
+ *   h       : the factorization (its N, k, eta define A)
+ *   points, normals, weights : device, the arrays the factorization was
+ *             computed from (caller order, as for fmmlu_factor)
+ *   b, x    : device complex128, N x nrhs column-major; x must not alias b;
+ *             each column is solved on its own
+ *   tol     : in (0, 1): stop when the residual estimate <= tol ||b||
+ *   restart : Krylov vectors per cycle, 1..64
+ *   maxiter : total steps per column, >= 1
+ *   iters   : host, nrhs ints (may be NULL): steps taken per column
+ *   relres  : host, nrhs doubles (may be NULL): true ||b - A x|| / ||b||
+ *             per column, from one more product after the last step
+ * Synchronises the stream once per step. Work memory: (N x 69 + small)
+ * complex128, allocated and freed by the call. Errors: INVALID_ARG, OOM,
+ * CUDA, NOT_CONVERGED (some column's estimate stayed above tol; x, iters
+ * and relres hold the last iterate). */
+int fmmlu_gmres(const fmmlu_handle* h, const double* points, const double* normals,
+                const double* weights, const double* b, double* x, int nrhs, double tol,
+                int restart, int maxiter, int* iters, double* relres, void* stream);
+
+/* Sound-soft boundary data of incident plane waves exp(i k d.x) (Sec. 6.3):
+ * b[j + m N] = -sqrt(w_j) exp(i k d_m . x_j), the right-hand sides of the
+ * sqrt(w)-scaled system for m = 0 .. m-1.
+ *   points, weights : device, caller order (N x 3, N)
+ *   dirs            : device, m x 3 row-major unit propagation directions
+ *   b               : device complex128, N x m column-major (written)
+ * Errors: INVALID_ARG, CUDA. */
+int fmmlu_plane_waves(int64_t n, const double* points, const double* weights, double k,
+                      const double* dirs, int m, double* b, void* stream);
+
+/* Monostatic (backscattered) far-field pattern of the combined-field layer
+ * potential of each column of x (Sec. 6.3, sonar cross section): for the
+ * plane wave travelling along d_m, with u = e^{ikr}/r F + O(1/r^2),
+ *   R_m = F(-d_m) = (1/(4 pi)) sum_j sqrt(w_j) x_{j,m} exp(i k d_m.x_j)
+ *                   (i k n_j.d_m - i eta),
+ * which for eta = k is (-i k/(4 pi)) sum_j sqrt(w_j) x_{j,m}
+ * exp(i k d_m.x_j) (1 - n_j.d_m). x holds the solutions x~ = sqrt(w) sigma.
+ *   points, normals, weights : device, caller order; eta NaN means k
+ *   dirs : device, m x 3 row-major unit directions of incidence
+ *   x    : device complex128, N x m column-major
+ *   R    : device complex128, m values (written)
+ * Synchronises the stream. Errors: INVALID_ARG, OOM, CUDA. */
+int fmmlu_backscatter(int64_t n, const double* points, const double* normals,
+                      const double* weights, double k, double eta, const double* dirs, int m,
+                      const double* x, double* R, void* stream);
+
+/* Sonar cross-section sweep (Sec. 6.3): for every direction d_m the plane
+ * wave's right-hand side, the solve with the stored factors (batches of
+ * `batch` right-hand sides per solve, at most 1024) and the backscattered
+ * far field R_m as in fmmlu_backscatter, with the handle's k and eta.
+ *   points, normals, weights : device, the factorization's arrays
+ *   dirs  : device, m x 3 row-major unit directions (azimuthal sweep:
+ *           d_m = (cos phi_m, sin phi_m, 0))
+ *   R     : device complex128, m values (written)
+ * Work memory N x batch complex128, allocated and freed by the call.
+ * Synchronises the stream. Errors: INVALID_ARG, OOM, CUDA. */
+int fmmlu_sonar_sweep(const fmmlu_handle* h, const double* points, const double* normals,
+                      const double* weights, const double* dirs, int m, int batch, double* R,
+                      void* stream);
 
 /* Write a JSON object with the factorization statistics into `json` (host,
  * capacity `cap` bytes, always NUL-terminated when cap > 0): N, levels, n0,

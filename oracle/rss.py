@@ -165,11 +165,33 @@ class Factorization:
         return int(self.root_dofs.size)
 
 
-def proxy_points(tree, box, n_proxy: int, proxy_factor: float):
+def proxy_count(k: float, rho: float, eps: float, n_min: int) -> int:
+    """Frequency-adaptive number of proxy points (Sec. 5.2, proxy surface
+    discretization: choose n_gamma from multipole estimates). Reading: the
+    excess-bandwidth estimate of the truncation degree of a multipole
+    expansion on a sphere of radius rho at accuracy eps,
+        p = ceil(k rho + 1.8 d0^(2/3) (k rho)^(1/3)),  d0 = log10(1/eps),
+    and twice the (p + 1)^2 spherical harmonics of degree <= p as sample
+    points, never fewer than n_min."""
+    kr = k * rho
+    d0 = math.log10(1.0 / eps)
+    p = math.ceil(kr + 1.8 * d0 ** (2.0 / 3.0) * kr ** (1.0 / 3.0))
+    return max(int(n_min), 2 * (p + 1) ** 2)
+
+
+def proxy_points(tree, box, n_proxy: int, proxy_factor: float, rule: str = "fixed",
+                 k: float = 0.0, eps: float = 1.0):
+    """Proxy sphere of `box`: centre of the box, radius proxy_factor x its
+    half-diagonal, Fibonacci points. rule "fixed": n_proxy points; rule
+    "adaptive": proxy_count(k, rho, eps, n_proxy) points."""
     b = tree.boxes[box]
     h = tree.side / float(1 << b.level)
     center = tree.corner + (np.array(b.cell, dtype=np.float64) + 0.5) * h
     rho = proxy_factor * (math.sqrt(3.0) / 2.0) * h
+    if rule == "adaptive":
+        n_proxy = proxy_count(k, rho, eps, n_proxy)
+    elif rule != "fixed":
+        raise ValueError(rule)
     return center[None, :] + rho * fibonacci_sphere(n_proxy), rho
 
 
@@ -211,7 +233,7 @@ def strong_skeletonize(A, R, S, nd, T):
 
 def factor(points, normals, weights, k, eps, eta=None, leaf_size=64,
            n_proxy=300, proxy_factor=1.5, tree=None, record=None,
-           snapshot_far=False):
+           snapshot_far=False, proxy_rule="fixed"):
     """RS-S factorization of the scaled CFIE system. Returns a Factorization.
 
     `record` (a list) receives one dict per processed box; with
@@ -258,7 +280,7 @@ def factor(points, normals, weights, k, eps, eta=None, leaf_size=64,
             a = act[B]
             nd = np.concatenate([act[C] for C in L.near[B]] or [empty])
             qd = np.concatenate([act[C] for C in L.farq[B]] or [empty])
-            Y, rho = proxy_points(tr, B, n_proxy, proxy_factor)
+            Y, rho = proxy_points(tr, B, n_proxy, proxy_factor, proxy_rule, k, eps)
             M = id_matrix(A, a, qd, x, nrm, sw, k, eta, Y, rho)
             pv, s, T = interp_decomp(M, eps)
             S = a[pv[:s]]

@@ -20,10 +20,11 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfmmlu.so")
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "SINGULAR_PIVOT",
-    -5: "NONFINITE", -6: "DEPTH_CAP", -7: "TIMEOUT", -8: "LIMIT",
+    -5: "NONFINITE", -6: "DEPTH_CAP", -7: "TIMEOUT", -8: "LIMIT", -9: "NOT_CONVERGED",
 }
 PRECISION_AUTO, PRECISION_FP64, PRECISION_MIXED = 0, 1, 2
 ID_AUTO, ID_HOUSEHOLDER, ID_GRAM = 0, 1, 2
+PROXY_FIXED, PROXY_ADAPTIVE = 0, 1
 
 
 class FmmluError(RuntimeError):
@@ -50,6 +51,7 @@ class fmmlu_opts(ctypes.Structure):
         ("solve_graph", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("autotune_cache", ctypes.c_char_p),
+        ("proxy_rule", ctypes.c_int),
     ]
 
 
@@ -92,6 +94,15 @@ def load_library(path: str | None = None):
     lib.fmmlu_profile_reset.restype = ci
     lib.fmmlu_solve_noalloc.argtypes = [vp, vp, vp, ci, ci, vp]
     lib.fmmlu_solve_noalloc.restype = ci
+    lib.fmmlu_gmres.argtypes = [vp, vp, vp, vp, vp, vp, ci, dbl, ci, ci,
+                                ctypes.POINTER(ci), ctypes.POINTER(dbl), vp]
+    lib.fmmlu_gmres.restype = ci
+    lib.fmmlu_plane_waves.argtypes = [i64, vp, vp, dbl, vp, ci, vp, vp]
+    lib.fmmlu_plane_waves.restype = ci
+    lib.fmmlu_backscatter.argtypes = [i64, vp, vp, vp, dbl, dbl, vp, ci, vp, vp, vp]
+    lib.fmmlu_backscatter.restype = ci
+    lib.fmmlu_sonar_sweep.argtypes = [vp, vp, vp, vp, vp, ci, ci, vp, vp]
+    lib.fmmlu_sonar_sweep.restype = ci
     lib.fmmlu_free.argtypes = [vp]
     lib.fmmlu_free.restype = None
     lib.fmmlu_last_error.argtypes = []
@@ -213,6 +224,81 @@ def fmmlu_matvec(points, normals, weights, k: float, eta: float, v: torch.Tensor
                                        weights.data_ptr(), float(k), float(eta),
                                        v.data_ptr(), y.data_ptr(), nrhs, _stream(stream)))
     return y
+
+
+def fmmlu_gmres(handle, points, normals, weights, b: torch.Tensor, x: torch.Tensor, n: int,
+                tol: float = 1e-10, restart: int = 30, maxiter: int = 200, stream=None):
+    """GMRES preconditioned by the factorization; returns (iters, relres,
+    converged) with one entry of iters and relres per column."""
+    _dev(points, torch.float64, "points")
+    _dev(normals, torch.float64, "normals")
+    _dev(weights, torch.float64, "weights")
+    b, nrhs = _cols(b, n, "b")
+    x, nrhs2 = _cols(x, n, "x")
+    if nrhs != nrhs2:
+        raise ValueError("b and x must have the same number of columns")
+    its = (ctypes.c_int * nrhs)()
+    rel = (ctypes.c_double * nrhs)()
+    rc = load_library().fmmlu_gmres(handle, points.data_ptr(), normals.data_ptr(),
+                                    weights.data_ptr(), b.data_ptr(), x.data_ptr(), nrhs,
+                                    float(tol), int(restart), int(maxiter), its, rel,
+                                    _stream(stream))
+    if rc not in (0, -9):
+        _check(rc)
+    return list(its), list(rel), rc == 0
+
+
+def _dirs(dirs: torch.Tensor) -> int:
+    _dev(dirs, torch.float64, "dirs")
+    if dirs.dim() != 2 or dirs.shape[1] != 3:
+        raise ValueError("dirs must be (m, 3)")
+    return int(dirs.shape[0])
+
+
+def fmmlu_plane_waves(points, weights, k: float, dirs: torch.Tensor, b: torch.Tensor,
+                      stream=None):
+    """b (m, n) complex128 (column-major n x m) = -sqrt(w) exp(i k d_m . x)."""
+    n = points.shape[0]
+    _dev(points, torch.float64, "points")
+    _dev(weights, torch.float64, "weights")
+    m = _dirs(dirs)
+    b, nb = _cols(b, n, "b")
+    if nb != m:
+        raise ValueError("b must have one column per direction")
+    _check(load_library().fmmlu_plane_waves(n, points.data_ptr(), weights.data_ptr(), float(k),
+                                            dirs.data_ptr(), m, b.data_ptr(), _stream(stream)))
+    return b
+
+
+def fmmlu_backscatter(points, normals, weights, k: float, eta: float, dirs: torch.Tensor,
+                      x: torch.Tensor, R: torch.Tensor, stream=None):
+    n = points.shape[0]
+    for t, nm in ((points, "points"), (normals, "normals"), (weights, "weights")):
+        _dev(t, torch.float64, nm)
+    m = _dirs(dirs)
+    x, nx = _cols(x, n, "x")
+    _dev(R, torch.complex128, "R")
+    if nx != m or R.numel() != m:
+        raise ValueError("x and R must have one column / entry per direction")
+    _check(load_library().fmmlu_backscatter(n, points.data_ptr(), normals.data_ptr(),
+                                            weights.data_ptr(), float(k), float(eta),
+                                            dirs.data_ptr(), m, x.data_ptr(), R.data_ptr(),
+                                            _stream(stream)))
+    return R
+
+
+def fmmlu_sonar_sweep(handle, points, normals, weights, dirs: torch.Tensor, R: torch.Tensor,
+                      batch: int = 64, stream=None):
+    for t, nm in ((points, "points"), (normals, "normals"), (weights, "weights")):
+        _dev(t, torch.float64, nm)
+    m = _dirs(dirs)
+    _dev(R, torch.complex128, "R")
+    if R.numel() != m:
+        raise ValueError("R must have one entry per direction")
+    _check(load_library().fmmlu_sonar_sweep(handle, points.data_ptr(), normals.data_ptr(),
+                                            weights.data_ptr(), dirs.data_ptr(), m, int(batch),
+                                            R.data_ptr(), _stream(stream)))
+    return R
 
 
 def fmmlu_stats(handle) -> dict:

@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfmmlu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["capi.cu", "tree.cu", "assembly.cu", "linalg.cu", "solve.cu", "prof.cu", "cpqr_dist.cu", "gj_dist.cu", "ozaki.cu", "pchol.cu", "tcgemm.cu"]
+SOURCES = ["capi.cu", "tree.cu", "assembly.cu", "linalg.cu", "solve.cu", "prof.cu", "cpqr_dist.cu", "gj_dist.cu", "ozaki.cu", "pchol.cu", "tcgemm.cu", "krylov.cu", "sonar.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", SRC]

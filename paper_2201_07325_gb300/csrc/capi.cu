@@ -160,6 +160,7 @@ void default_opts(fmmlu_opts* o) {
   o->eta = NAN;
   o->proxy_radius_factor = 1.5;
   o->n_proxy = 300;
+  o->proxy_rule = FMMLU_PROXY_FIXED;
   o->precision = FMMLU_PRECISION_AUTO;
   o->eps_id_divisor = 1.0;
   o->verbose = 0;
@@ -182,6 +183,8 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (!(o.proxy_radius_factor > 1.0 && o.proxy_radius_factor < 2.88))
     throw Error(FMMLU_ERR_INVALID_ARG, "proxy_radius_factor must lie in (1, 2.88)");
   if (o.n_proxy < 8 || o.n_proxy > 100000) throw Error(FMMLU_ERR_INVALID_ARG, "n_proxy out of [8, 100000]");
+  if (o.proxy_rule != FMMLU_PROXY_FIXED && o.proxy_rule != FMMLU_PROXY_ADAPTIVE)
+    throw Error(FMMLU_ERR_INVALID_ARG, "proxy_rule must be FMMLU_PROXY_FIXED or FMMLU_PROXY_ADAPTIVE");
   if (o.precision < 0 || o.precision > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad precision");
   if (!(o.eps_id_divisor > 0.0)) throw Error(FMMLU_ERR_INVALID_ARG, "eps_id_divisor must be > 0");
   if (o.id_method < 0 || o.id_method > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad id_method");
@@ -579,6 +582,20 @@ std::shared_ptr<SolvePlan> make_solve_plan(const fmmlu_handle* H, int chunk, cud
   return P;
 }
 
+// Proxy points per sphere of radius rho (Sec. 5.2: n_gamma from multipole
+// estimates). Adaptive rule: the excess-bandwidth truncation degree
+// p = ceil(k rho + 1.8 d^(2/3) (k rho)^(1/3)), d = log10(1/eps), and
+// 2 (p + 1)^2 points (twice the spherical harmonics of degree <= p), at least
+// n_proxy.
+int proxy_count_for(const fmmlu_opts& opt, double k, double rho, double eps) {
+  if (opt.proxy_rule != FMMLU_PROXY_ADAPTIVE) return opt.n_proxy;
+  const double kr = k * rho, d0 = std::log10(1.0 / eps);
+  const double p = std::ceil(kr + 1.8 * std::pow(d0, 2.0 / 3.0) * std::pow(kr, 1.0 / 3.0));
+  const double cnt = 2.0 * (p + 1.0) * (p + 1.0);
+  if (!(cnt < 1e6)) throw Error(FMMLU_ERR_LIMIT, "adaptive proxy count above 10^6 points");
+  return std::max(opt.n_proxy, (int)cnt);
+}
+
 void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, const double* w,
                  double k, double eps, const fmmlu_opts& opt, cudaStream_t st, fmmlu_handle* H) {
   const TreeHost& T = tree->T;
@@ -641,6 +658,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       prev = std::move(L);
       break;
     }
+    // proxy points of this level's spheres (Sec. 5.2)
+    const double hlev = T.side / (double)(1 << lev);
+    const int nprox = proxy_count_for(opt, k, opt.proxy_radius_factor * 0.86602540378443864676 * hlev,
+                                      eps_id);
     // descriptors in elimination order
     std::vector<BoxDesc> desc(nb);
     std::vector<int> nlist, qlist;
@@ -672,7 +693,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         qlist.push_back(c);
         d.qmax += L->a0[c];
       }
-      d.mmax = 2 * d.qmax + 2 * opt.n_proxy;
+      d.mmax = 2 * d.qmax + 2 * nprox;
       d.h = hreal;
       d.cx = T.corner[0] + ((double)hb.cx + 0.5) * hreal;
       d.cy = T.corner[1] + ((double)hb.cy + 0.5) * hreal;
@@ -746,7 +767,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     LD.Wbuf = lw.get<double2>((size_t)W_max);
     LD.arena = d_arena;
     LD.iarena = d_iarena;
-    LD.n_proxy = opt.n_proxy;
+    LD.n_proxy = nprox;
     LD.proxy_factor = opt.proxy_radius_factor;
     LD.eps = eps_id;
     LD.status = d_status;
@@ -1155,7 +1176,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         const BoxDesc& d = desc[e];
         const BoxRun& rr = run[e];
         double a = d.a, s_ = rr.s, r_ = rr.r, n_ = rr.n;
-        double m = 2.0 * rr.nq + 2.0 * opt.n_proxy;
+        double m = 2.0 * rr.nq + 2.0 * nprox;
         // one kernel evaluation per entry of M, kKevalFlops real flops each
         // (besides the exponential); the outgoing and incoming rows of a pair
         // share one distance and one exp(ikr)
@@ -1285,7 +1306,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
                    (long long)max_a, (long long)max_r, L->pool_size * 16.0 / 1e6, lms, ns_boxes,
                    ns_worst, ns_fallback);
     js << (first_level ? "" : ", ") << "{\"level\": " << lev << ", \"boxes\": " << nb
-       << ", \"colours\": " << HL.ncolours << ", \"current\": " << L->cur.size()
+       << ", \"colours\": " << HL.ncolours << ", \"n_proxy\": " << nprox
+       << ", \"current\": " << L->cur.size()
        << ", \"sum_a\": " << sum_a << ", \"sum_s\": " << sum_s << ", \"max_a\": " << max_a
        << ", \"max_r\": " << max_r << ", \"refined_inverses\": " << ns_boxes
        << ", \"refine_fallbacks\": " << ns_fallback << ", \"ms\": " << lms << "}";
@@ -1584,6 +1606,118 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
   }
 }
 
+// ---------------------------------------------------------------------------
+// GMRES preconditioned by the stored factors (Sec. 7): A M^{-1} u = b,
+// x = M^{-1} u, M^{-1} = fmmlu_solve, A = the dense on-the-fly product.
+// ---------------------------------------------------------------------------
+
+struct GmresResult {
+  int iters = 0;
+  double relres = 0.0;     // true ||b - A x|| / ||b|| at the end
+  bool converged = false;  // the Givens estimate reached tol
+};
+
+void gmres_impl(const fmmlu_handle* H, const double* pts, const double* nrm, const double* wts,
+                const double2* b, double2* x, double tol, int restart, int maxiter,
+                cudaStream_t st, GmresResult& res) {
+  const int64_t n = H->n;
+  DevPool mem;
+  std::vector<int> iota((size_t)n);
+  std::iota(iota.begin(), iota.end(), 0);
+  int* d_id = mem.up(iota, st);
+  double* soa = mem.get<double>((size_t)n * 8);
+  launch_permute_geometry(pts, nrm, wts, d_id, n, soa, st);
+  Geometry g{soa, soa + n, soa + 2 * n, soa + 3 * n, soa + 4 * n, soa + 5 * n, soa + 6 * n,
+             soa + 7 * n, H->k, H->eta};
+  const int ldh = kKrMaxBasis;
+  double2* V = mem.get<double2>((size_t)n * kKrMaxBasis);
+  double2* w = mem.get<double2>((size_t)n);
+  double2* u = mem.get<double2>((size_t)n);
+  double2* z = mem.get<double2>((size_t)n);
+  double2* Hm = mem.get<double2>((size_t)ldh * kKrMaxRestart);
+  double2* hc = mem.get<double2>(kKrMaxBasis);
+  double2* gv = mem.get<double2>(kKrMaxBasis);
+  double2* yv = mem.get<double2>(kKrMaxBasis);
+  double2* nr = mem.get<double2>(kKrMaxBasis);
+  double* cs = mem.get<double>(kKrMaxRestart);
+  double2* sn = mem.get<double2>(kKrMaxRestart);
+  double* scal = mem.get<double>(2);
+  double* est = mem.get<double>(2);
+  double2* part = mem.get<double2>((size_t)kr_blocks(n) * kKrMaxBasis);
+  struct Pinned {
+    double* p = nullptr;
+    ~Pinned() { if (p) cudaFreeHost(p); }
+  } hest;
+  CK(cudaMallocHost(&hest.p, 2 * sizeof(double)));
+  auto read_est = [&]() {
+    CK(cudaMemcpyAsync(hest.p, est, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  };
+  auto norm2_into = [&](const double2* v) {   // nr[0] = (||v||^2, 0)
+    launch_kr_dots(v, n, 1, v, n, part, nr, nullptr, st);
+  };
+  auto apply_a = [&](const double2* v, double2* y) { launch_matvec(g, n, v, y, 1, st); };
+  auto apply_minv = [&](const double2* v, double2* y) {
+    solve_impl(H, reinterpret_cast<const double*>(v), reinterpret_cast<double*>(y), 1, false, st);
+  };
+  CK(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double2), st));
+  norm2_into(b);
+  launch_kr_start(nr, gv, kKrMaxBasis, scal, est, st);
+  read_est();
+  const double bnorm = hest.p[0];
+  res = GmresResult{};
+  if (!(bnorm > 0.0)) {
+    res.converged = true;
+    return;
+  }
+  int its = 0;
+  while (its < maxiter && !res.converged) {
+    // r = b - A x, beta = ||r||, V[:, 0] = r / beta
+    apply_a(x, u);
+    launch_kr_residual(w, b, u, n, st);
+    norm2_into(w);
+    launch_kr_start(nr, gv, kKrMaxBasis, scal, est, st);
+    read_est();
+    if (hest.p[0] <= tol * bnorm) {
+      res.converged = true;
+      break;
+    }
+    launch_kr_scale(V, w, scal, n, st);
+    const int m = std::min(restart, maxiter - its);
+    CK(cudaMemsetAsync(Hm, 0, sizeof(double2) * (size_t)ldh * kKrMaxRestart, st));
+    int jd = 0;
+    for (int j = 0; j < m; ++j) {
+      apply_minv(V + (int64_t)j * n, z);
+      apply_a(z, w);
+      double2* Hj = Hm + (int64_t)j * ldh;
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        launch_kr_dots(V, n, j + 1, w, n, part, hc, Hj, st);
+        launch_kr_update(w, V, n, j + 1, hc, n, st);
+      }
+      norm2_into(w);
+      launch_kr_givens(Hm, ldh, j, nr, cs, sn, gv, scal, est, st);
+      launch_kr_scale(V + (int64_t)(j + 1) * n, w, scal, n, st);
+      ++its;
+      jd = j + 1;
+      read_est();
+      if (hest.p[0] <= tol * bnorm) res.converged = true;
+      if (res.converged || hest.p[1] == 0.0) break;
+    }
+    launch_kr_trisolve(Hm, ldh, jd, gv, yv, st);
+    launch_kr_combine(u, V, n, jd, yv, n, st);
+    apply_minv(u, z);
+    launch_kr_add(x, z, n, st);
+  }
+  // true residual of the result
+  apply_a(x, u);
+  launch_kr_residual(w, b, u, n, st);
+  norm2_into(w);
+  launch_kr_start(nr, gv, kKrMaxBasis, scal, est, st);
+  read_est();
+  res.iters = its;
+  res.relres = hest.p[0] / bnorm;
+}
+
 inline size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Work-space layout of fmmlu_solve_noalloc for one (nrhs, direction): the
@@ -1753,6 +1887,98 @@ int fmmlu_matvec(int64_t n, const double* points, const double* normals, const d
                   st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
+  });
+}
+
+int fmmlu_gmres(const fmmlu_handle* h, const double* points, const double* normals,
+                const double* weights, const double* b, double* x, int nrhs, double tol,
+                int restart, int maxiter, int* iters, double* relres, void* stream) {
+  return guard([&] {
+    if (!h || h->magic != kHandleMagic || !points || !normals || !weights || !b || !x ||
+        nrhs < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, or nrhs < 1");
+    if (b == x) throw Error(FMMLU_ERR_INVALID_ARG, "x must not alias b");
+    if (!(tol > 0.0 && tol < 1.0)) throw Error(FMMLU_ERR_INVALID_ARG, "tol must lie in (0, 1)");
+    if (restart < 1 || restart > kKrMaxRestart)
+      throw Error(FMMLU_ERR_INVALID_ARG, "restart must lie in [1, 64]");
+    if (maxiter < 1) throw Error(FMMLU_ERR_INVALID_ARG, "maxiter must be >= 1");
+    check_device(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    bool all = true;
+    for (int c = 0; c < nrhs; ++c) {
+      GmresResult r;
+      gmres_impl(h, points, normals, weights,
+                 reinterpret_cast<const double2*>(b) + (int64_t)c * h->n,
+                 reinterpret_cast<double2*>(x) + (int64_t)c * h->n, tol, restart, maxiter, st, r);
+      if (iters) iters[c] = r.iters;
+      if (relres) relres[c] = r.relres;
+      all = all && r.converged;
+    }
+    if (!all)
+      throw Error(FMMLU_ERR_NOT_CONVERGED,
+                  "GMRES did not reach tol within maxiter steps (x holds the last iterate)");
+  });
+}
+
+int fmmlu_plane_waves(int64_t n, const double* points, const double* weights, double k,
+                      const double* dirs, int m, double* b, void* stream) {
+  return guard([&] {
+    if (n < 1 || !points || !weights || !dirs || !b || m < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, n < 1 or m < 1");
+    if (!(k > 0.0) || !std::isfinite(k)) throw Error(FMMLU_ERR_INVALID_ARG, "k must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int m0 = 0; m0 < m; m0 += 65535)
+      launch_plane_waves(points, weights, n, k, dirs, m0, std::min(65535, m - m0),
+                         reinterpret_cast<double2*>(b) + (int64_t)m0 * n, st);
+    CK(cudaGetLastError());
+  });
+}
+
+int fmmlu_backscatter(int64_t n, const double* points, const double* normals,
+                      const double* weights, double k, double eta, const double* dirs, int m,
+                      const double* x, double* R, void* stream) {
+  return guard([&] {
+    if (n < 1 || !points || !normals || !weights || !dirs || !x || !R || m < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, n < 1 or m < 1");
+    if (!(k > 0.0) || !std::isfinite(k)) throw Error(FMMLU_ERR_INVALID_ARG, "k must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevPool w;
+    const int mb = std::min(m, 65535);
+    double2* part = w.get<double2>((size_t)backscatter_blocks(n) * mb);
+    for (int m0 = 0; m0 < m; m0 += mb)
+      launch_backscatter(points, normals, weights, n, k, std::isnan(eta) ? k : eta, dirs, m0,
+                         std::min(mb, m - m0),
+                         reinterpret_cast<const double2*>(x) + (int64_t)m0 * n, part,
+                         reinterpret_cast<double2*>(R), st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));   // the partial sums are freed on return
+  });
+}
+
+int fmmlu_sonar_sweep(const fmmlu_handle* h, const double* points, const double* normals,
+                      const double* weights, const double* dirs, int m, int batch, double* R,
+                      void* stream) {
+  return guard([&] {
+    if (!h || h->magic != kHandleMagic || !points || !normals || !weights || !dirs || !R ||
+        m < 1 || batch < 1)
+      throw Error(FMMLU_ERR_INVALID_ARG, "null argument, not a handle, m < 1 or batch < 1");
+    check_device(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->n;
+    const int bs = std::min(std::min(batch, m), 1024);
+    DevPool w;
+    double2* b = w.get<double2>((size_t)n * bs);
+    double2* part = w.get<double2>((size_t)backscatter_blocks(n) * bs);
+    for (int m0 = 0; m0 < m; m0 += bs) {
+      const int c = std::min(bs, m - m0);
+      launch_plane_waves(points, weights, n, h->k, dirs + 3 * (int64_t)m0, 0, c, b, st);
+      solve_impl(h, reinterpret_cast<const double*>(b), reinterpret_cast<double*>(b), c, false,
+                 st);
+      launch_backscatter(points, normals, weights, n, h->k, h->eta, dirs + 3 * (int64_t)m0, 0,
+                         c, b, part, reinterpret_cast<double2*>(R) + m0, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));   // the work arrays are freed on return
   });
 }
 

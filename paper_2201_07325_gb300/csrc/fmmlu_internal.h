@@ -318,5 +318,33 @@ void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,
 size_t root_solve_scratch_bytes(int n0, int nb, int nrhs);
 cudaError_t launch_root_solve(const double2* A, int n0, int nb, double2* vr, double2* z,
                               void* scratch, int nrhs, bool adjoint, cudaStream_t st);
+// sonar.cu (plane waves and the backscattered far field, caller order)
+int backscatter_blocks(int64_t n);   // partial sums per direction
+void launch_plane_waves(const double* pts, const double* w, int64_t n, double k,
+                        const double* dirs, int m0, int mcount, double2* b, cudaStream_t st);
+void launch_backscatter(const double* pts, const double* nrm, const double* w, int64_t n,
+                        double k, double eta, const double* dirs, int m0, int mcount,
+                        const double2* x, double2* part, double2* R, cudaStream_t st);
+// krylov.cu (preconditioned GMRES: basis of at most kKrMaxRestart + 1 vectors)
+constexpr int kKrMaxRestart = 64;
+constexpr int kKrMaxBasis = kKrMaxRestart + 1;
+int kr_blocks(int64_t n);   // partial sums per inner product (size of `part` / ncols)
+void launch_kr_dots(const double2* V, int64_t ldv, int ncols, const double2* w, int64_t n,
+                    double2* part, double2* hc, double2* hacc, cudaStream_t st);
+void launch_kr_update(double2* w, const double2* V, int64_t ldv, int ncols, const double2* hc,
+                      int64_t n, cudaStream_t st);
+void launch_kr_scale(double2* dst, const double2* src, const double* scal, int64_t n,
+                     cudaStream_t st);
+void launch_kr_residual(double2* r, const double2* b, const double2* y, int64_t n,
+                        cudaStream_t st);
+void launch_kr_add(double2* x, const double2* z, int64_t n, cudaStream_t st);
+void launch_kr_combine(double2* u, const double2* V, int64_t ldv, int ncols, const double2* y,
+                       int64_t n, cudaStream_t st);
+void launch_kr_givens(double2* H, int ldh, int j, const double2* nrm2, double* cs, double2* sn,
+                      double2* g, double* scal, double* est, cudaStream_t st);
+void launch_kr_start(const double2* nrm2, double2* g, int len, double* scal, double* est,
+                     cudaStream_t st);
+void launch_kr_trisolve(const double2* H, int ldh, int jd, const double2* g, double2* y,
+                        cudaStream_t st);
 
 }  // namespace fmmlu

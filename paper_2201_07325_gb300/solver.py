@@ -69,6 +69,25 @@ class Factorization:
         B.fmmlu_solve_adjoint(self.handle, bb, x, self.n)
         return x.t() if tr else x
 
+    def gmres(self, b, tol: float = 1e-10, restart: int = 30, maxiter: int = 200):
+        """x with A x = b by GMRES preconditioned by this factorization (Sec. 7);
+        returns (x, iters, relres, converged)."""
+        bb, tr = self._vec(b)
+        x = torch.empty_like(bb)
+        its, rel, ok = B.fmmlu_gmres(self.handle, self.points, self.normals, self.weights, bb, x,
+                                     self.n, tol, restart, maxiter)
+        return (x.t() if tr else x), its, rel, ok
+
+    def sonar_cross_section(self, phis, batch: int = 64):
+        """Monostatic backscattered far field R(phi) for incident plane waves
+        along d = (cos phi, sin phi, 0) (Sec. 6.3); returns complex128 (m,)."""
+        ph = torch.as_tensor(phis, dtype=torch.float64)
+        dirs = torch.stack([torch.cos(ph), torch.sin(ph), torch.zeros_like(ph)], dim=1)
+        dirs = dirs.to(self.device).contiguous()
+        R = torch.empty(dirs.shape[0], dtype=torch.complex128, device=self.device)
+        B.fmmlu_sonar_sweep(self.handle, self.points, self.normals, self.weights, dirs, R, batch)
+        return R
+
     def matvec(self, v):
         """A v by the dense on-the-fly product (independent of the factors)."""
         vv, tr = self._vec(v)

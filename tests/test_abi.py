@@ -91,7 +91,8 @@ def test_solve_and_tuning_options(lib):
     assert o.autotune_cache is None
     out = ctypes.c_void_p()
     for field, value in (("solve_chunk", 40), ("solve_chunk", 8192), ("solve_graph", 3),
-                         ("autotune", 2), ("schur_emulation", 3), ("id_method", -1)):
+                         ("autotune", 2), ("schur_emulation", 3), ("id_method", -1),
+                         ("proxy_rule", 2)):
         bad = pkg.fmmlu_default_opts(**{field: value})
         rc = lib.fmmlu_build_tree(ctypes.c_void_p(8), 10, ctypes.byref(bad), None,
                                   ctypes.byref(out))

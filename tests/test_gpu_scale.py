@@ -203,20 +203,24 @@ def test_autograd_on_config_subset(pkg, sphere4k):
 # ---------------------------------------------------------------------------
 
 FULL = [
-    # workload, precision, rows sampled
-    ("ellipsoid1m", "mixed", 384),
-    ("sphere100k", "fp64", 1500),
+    # workload, precision, proxy rule and floor (the benchmark's), rows sampled
+    ("ellipsoid1m", "mixed", "adaptive", 64, 384),
+    ("ellipsoid1m", "mixed", "fixed", 300, 256),
+    ("sphere100k", "fp64", "fixed", 300, 1500),
 ]
 
 
-@pytest.mark.parametrize("name,prec,nrows", FULL, ids=[f[0] for f in FULL])
-def test_full_size_sampled_residuals(pkg, name, prec, nrows):
+@pytest.mark.parametrize("name,prec,rule,npx,nrows", FULL,
+                         ids=[f"{f[0]}-{f[2]}" for f in FULL])
+def test_full_size_sampled_residuals(pkg, name, prec, rule, npx, nrows):
     spec = synth.WORKLOADS[name]
     k, eps = spec["k"], spec["eps"]
     s = synth.make_surface(name)
     Bm = synth.make_rhs(name, s)                                   # (n, nrhs)
     P = pkg.PRECISION_MIXED if prec == "mixed" else pkg.PRECISION_FP64
-    fac = pkg.Factorization(s.points, s.normals, s.weights, k, eps, leaf_size=64, precision=P)
+    fac = pkg.Factorization(s.points, s.normals, s.weights, k, eps, leaf_size=64, precision=P,
+                            n_proxy=npx,
+                            proxy_rule=pkg.PROXY_ADAPTIVE if rule == "adaptive" else pkg.PROXY_FIXED)
     try:
         st = fac.stats()
         assert st["precision"] == prec

@@ -240,3 +240,30 @@ def test_proxy_sphere_near_the_far_boundary(ell):
     s28 = sum(r["S"].size for r in rec)
     s15 = sum(r["S"].size for r in rec15)
     assert abs(s28 - s15) <= 0.15 * s15
+
+
+def test_adaptive_proxy_count_rule():
+    """The multipole estimate of the proxy count (Sec. 5.2): the floor for
+    small boxes, growth with k rho, with the digits of accuracy, and the
+    degree estimate p = ceil(k rho + 1.8 d^(2/3) (k rho)^(1/3)) at a value
+    worked by hand: k rho = 8, eps = 1e-6 -> p = ceil(8 + 1.8 * 3.3019 * 2)
+    = 20, 2 (p + 1)^2 = 882."""
+    assert rss.proxy_count(1.0, 1e-3, 1e-6, 300) == 300
+    assert rss.proxy_count(8.0, 1.0, 1e-6, 24) == 882
+    counts = [rss.proxy_count(k, 0.5, 1e-6, 24) for k in (1.0, 4.0, 16.0, 64.0)]
+    assert counts == sorted(counts) and counts[-1] > counts[0]
+    assert rss.proxy_count(16.0, 0.5, 1e-10, 24) > rss.proxy_count(16.0, 0.5, 1e-3, 24)
+
+
+def test_adaptive_proxy_ids_against_dense_far_field(ell):
+    """With the per-level multipole count (floor 24 points) every ID still
+    meets 10 eps against the explicit far field and the solution is within
+    10 eps; the coarse levels use more points than the fine ones."""
+    s, A, b, xd, T = ell
+    eps = 1e-4
+    F, rec = _factor(ell, eps, n_proxy=24, proxy_rule="adaptive")
+    worst, count = _id_error_ratio(rec, eps)
+    assert count > 20 and worst <= 10.0
+    x = rss.solve(F, b)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= 10 * eps
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 10 * eps
