@@ -511,6 +511,12 @@ def run_gpu(args, rank, world):
         "gpu_launches_per_step": launches / max(1, args.steps),
         "roofline": roof,
         "top_kernels": {nm: roofs[nm] for nm in order[:10]},
+        "profiled_step": {"ms": prof_step_ms,
+                          "kernel_ms": sum(e["ms"] for e in kern.values()),
+                          "launches": sum(e["launches"] for e in kern.values()),
+                          "idle_fraction": 1.0 - sum(e["ms"] for e in kern.values()) / prof_step_ms,
+                          "kernel_ms_by_class": {nm: e["ms"] for nm, e in
+                                                 sorted(kern.items(), key=lambda kv: -kv[1]["ms"])}},
         "clocks": clocks,
     }
     # ---- plain fp64 at the same eps, and the other workloads ---------------
@@ -534,6 +540,35 @@ def run_gpu(args, rank, world):
             del wa
             torch.cuda.empty_cache()
         log("arms done")
+        # the azimuthal sonar sweep (Sec. 6.3): factor, then plane waves,
+        # batched solves and backscattered far fields for every angle
+        log("sonar sweep")
+        ws = Workload("sonar200k", dev) if args.workload != "sonar200k" else w
+        osn = pkg.fmmlu_default_opts(leaf_size=64, precision=pkg.PRECISION_AUTO,
+                                     **proxy_opts("sonar200k"))
+        phis = synth.azimuthal_angles(synth.WORKLOADS["sonar200k"]["angles"])
+        dirs = torch.from_numpy(np.stack([np.cos(phis), np.sin(phis), np.zeros_like(phis)],
+                                         axis=1)).to(dev)
+        Rs = torch.empty(len(phis), dtype=torch.complex128, device=dev)
+        for rep in range(2):
+            torch.cuda.synchronize()
+            e0.record(st)
+            t = pkg.fmmlu_build_tree(ws.pts, osn)
+            hs = pkg.fmmlu_factor(t, ws.pts, ws.nrm, ws.wts, ws.k, ws.eps, osn)
+            pkg.fmmlu_free(t)
+            e1.record(st)
+            e2 = torch.cuda.Event(enable_timing=True)
+            pkg.fmmlu_sonar_sweep(hs, ws.pts, ws.nrm, ws.wts, dirs, Rs, 32)
+            e2.record(st)
+            torch.cuda.synchronize()
+            pkg.fmmlu_free(hs)
+        extra["sonar200k_sweep"] = {
+            "workload": "sonar200k", "n": ws.n, "k": ws.k, "eps": ws.eps, "angles": len(phis),
+            "batch": 32, "t_tree_factor_s": e0.elapsed_time(e1) / 1e3,
+            "t_sweep_ms": e1.elapsed_time(e2), "angles_per_s": len(phis) / (e1.elapsed_time(e2) / 1e3),
+            "max_abs_R": float(Rs.abs().max())}
+        del ws
+        torch.cuda.empty_cache()
         plain = extra.pop(f"{args.workload}_fp64", None)
         if plain is not None:
             out["plain_fp64"] = plain
@@ -556,8 +591,8 @@ def run_gpu(args, rank, world):
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-BASELINE_SIZES = (2000, 4000)
-REFERENCE_N = 1200
+BASELINE_SIZES = (1000, 2000)
+REFERENCE_N = 800
 
 
 def oracle_step(workload: str, nsample: int):

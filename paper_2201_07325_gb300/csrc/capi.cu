@@ -1798,39 +1798,11 @@ int fmmlu_build_tree(const double* points, int64_t n, const fmmlu_opts* opts, vo
     *out = nullptr;
     fmmlu_opts o = checked_opts(opts);
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<double> p((size_t)n * 3);
-    CK(cudaMemcpyAsync(p.data(), points, p.size() * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    double lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
-    for (int64_t i = 0; i < n; ++i)
-      for (int a = 0; a < 3; ++a) {
-        double v = p[3 * i + a];
-        if (!std::isfinite(v)) throw Error(FMMLU_ERR_INVALID_ARG, "non-finite point coordinate");
-        lo[a] = std::min(lo[a], v);
-        hi[a] = std::max(hi[a], v);
-      }
     auto t = std::make_unique<fmmlu_tree>();
     t->opts = o;
-    TreeHost& T = t->T;
-    T.n = n;
-    double extent = 0;
-    double center[3];
-    for (int a = 0; a < 3; ++a) {
-      center[a] = (lo[a] + hi[a]) / 2.0;
-      extent = std::max(extent, hi[a] - lo[a]);
-    }
-    double side = extent * (1.0 + 1e-12);
-    if (!(side > 0.0)) side = 1.0;
-    T.side = side;
-    for (int a = 0; a < 3; ++a) T.corner[a] = center[a] - side / 2.0;
-    T.keys.resize(n);
-    T.perm.resize(n);
-    int rc = gpu_morton_sort(points, n, T.corner, side, T.keys.data(), T.perm.data(), st);
-    if (rc) throw Error(FMMLU_ERR_CUDA, std::string("morton sort: ") + cudaGetErrorString((cudaError_t)rc));
-    build_host_tree(T, o.leaf_size);
-    t->d_perm = dupload(T.perm, st);
-    CK(cudaStreamSynchronize(st));
+    std::string msg;
+    if (int rc = gpu_build_tree(points, n, o.leaf_size, t->T, &t->d_perm, msg, st))
+      throw Error(rc, "tree: " + msg);
     *out = t.release();
   });
 }

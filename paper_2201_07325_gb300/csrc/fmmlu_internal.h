@@ -152,10 +152,7 @@ void launch_end(const char* name, cudaStream_t st);
 // ---------------------------------------------------------------------------
 // launch wrappers (defined in the .cu files)
 // ---------------------------------------------------------------------------
-// tree.cu
-int gpu_morton_sort(const double* points_rowmajor, int64_t n, const double corner[3],
-                    double side, uint64_t* keys_out_host, int* perm_out_host,
-                    cudaStream_t st);
+// tree.cu: see tree_host.h (gpu_build_tree)
 // assembly.cu
 void launch_permute_geometry(const double* pts, const double* nrm, const double* w,
                              const int* perm, int64_t n, double* soa, cudaStream_t st);

@@ -1,9 +1,10 @@
-// Host-side octree description (built from GPU-sorted Morton keys).
+// Host-side description of the octree (built on the GPU by tree.cu).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <map>
 #include <stdint.h>
-#include <unordered_map>
+#include <string>
 #include <vector>
 
 namespace fmmlu {
@@ -34,18 +35,18 @@ struct TreeHost {
   double corner[3] = {0, 0, 0};
   double side = 1.0;
   std::vector<int> perm;           // sorted position -> caller index
-  std::vector<uint64_t> keys;      // sorted Morton keys
-  std::vector<HBox> boxes;
+  std::vector<HBox> boxes;         // ids ordered by (level, Morton)
   int nlevels = 0;
   int leaf_size = 64;
   std::map<int, HLevel> levels;    // l >= 2
-  std::unordered_map<uint64_t, int> where;   // (level, cell) -> id
 };
 
-void build_host_tree(TreeHost& T, int leaf_size);
-HLevel build_level(const TreeHost& T, int level);
+// Builds the whole tree on the GPU (tree.cu) from device points (N x 3
+// row-major) and fills T; *d_perm receives a device copy of the sorted
+// permutation (cudaFree by the caller). Returns 0 or a negative FMMLU_ERR_*
+// code with a message.
+int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int** d_perm,
+                   std::string& msg, cudaStream_t st);
 std::vector<int> current_boxes(const TreeHost& T, int level);
-int64_t box_gap(const HBox& a, const HBox& b);
-uint64_t morton3_host(int64_t cx, int64_t cy, int64_t cz);
 
 }  // namespace fmmlu

@@ -240,7 +240,15 @@ WORKLOADS = {
     "torus200k": dict(n=200000, k=5.0, eps=1e-4),
     "sphere100k": dict(n=100000, k=10.0, eps=1e-6),
     "ellipsoid1m": dict(n=1000000, k=20.0, eps=1e-4),
+    # azimuthal sonar sweep (Sec. 6.3) on a multiscale surface: 128 incident
+    # directions (cos phi, sin phi, 0), phi uniform in [0, 2 pi)
+    "sonar200k": dict(n=200000, k=10.0, eps=1e-4, angles=128),
 }
+
+
+def azimuthal_angles(m: int) -> np.ndarray:
+    """m incidence angles phi_j = 2 pi j / m of an azimuthal sweep."""
+    return 2.0 * math.pi * np.arange(m) / m
 
 
 def make_surface(name: str, n: int | None = None) -> Surface:
@@ -255,6 +263,8 @@ def make_surface(name: str, n: int | None = None) -> Surface:
         return torus_graded(n, seed=2203)
     if name == "ellipsoid1m":
         return ellipsoid_graded_tip(n, (1.0, 3.0, 0.5), seed=2205)
+    if name == "sonar200k":
+        return ellipsoid_graded_tip(n, (1.0, 3.0, 0.5), seed=2206)
     raise KeyError(name)
 
 
@@ -275,6 +285,11 @@ def make_rhs(name: str, surface: Surface, k: float | None = None) -> np.ndarray:
         return scaled_rhs(surface, f)
     if name == "ellipsoid1m":
         dirs = seeded_directions(16, 2205)
+        f = np.stack([-plane_wave(x, d, k) for d in dirs], axis=1)
+        return scaled_rhs(surface, f)
+    if name == "sonar200k":
+        ph = azimuthal_angles(spec["angles"])
+        dirs = np.stack([np.cos(ph), np.sin(ph), np.zeros_like(ph)], axis=1)
         f = np.stack([-plane_wave(x, d, k) for d in dirs], axis=1)
         return scaled_rhs(surface, f)
     raise KeyError(name)
