@@ -687,26 +687,45 @@ def run_reference(args, rank, world):
 
 
 def factor_once(args) -> dict:
-    """One tree + factorization of the workload (optionally at another size)
-    with per-launch profiling on: the small case the ncu captures run."""
+    """One tree + factorization of the workload (optionally at another size;
+    with --step-once also the solve and adjoint solve of its right-hand
+    sides), with per-launch profiling on: the case the ncu captures run.
+    Same options as the benchmark's step (leaf 64, the workload's proxy
+    rule)."""
     import torch
     import paper_2201_07325_gb300 as pkg
     pkg.load_library()
-    spec = synth.WORKLOADS[args.workload]
-    s = synth.make_surface(args.workload, args.n)
-    prec = {"fp64": pkg.PRECISION_FP64, "mixed": pkg.PRECISION_MIXED,
-            "auto": pkg.PRECISION_AUTO}[args.precision]
-    opts = pkg.fmmlu_default_opts(precision=prec, profile=1)
-    pts, nrm, w = (torch.from_numpy(np.ascontiguousarray(a)).cuda()
-                   for a in (s.points, s.normals, s.weights))
-    t = pkg.fmmlu_build_tree(pts, opts)
-    h = pkg.fmmlu_factor(t, pts, nrm, w, spec["k"], spec["eps"], opts)
+    w = Workload(args.workload, torch.device("cuda"), args.n)
+    rule, npx = args.proxy_rule, args.n_proxy
+    opts = pkg.fmmlu_default_opts(leaf_size=64, precision=precision_code(pkg, args.precision),
+                                  profile=1, n_proxy=npx,
+                                  proxy_rule=pkg.PROXY_ADAPTIVE if rule == "adaptive"
+                                  else pkg.PROXY_FIXED)
+    st = torch.cuda.current_stream()
+    if args.step_once:
+        # one unprofiled step first (the tuners run there), then the profiled
+        # step inside a profiler range (ncu --profile-from-start off)
+        opts0 = pkg.fmmlu_default_opts(leaf_size=64,
+                                       precision=precision_code(pkg, args.precision),
+                                       n_proxy=npx,
+                                       proxy_rule=pkg.PROXY_ADAPTIVE if rule == "adaptive"
+                                       else pkg.PROXY_FIXED)
+        pkg.fmmlu_free(gpu_step(pkg, w, opts0, st))
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        h = gpu_step(pkg, w, opts, st)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    else:
+        t = pkg.fmmlu_build_tree(w.pts, opts)
+        h = pkg.fmmlu_factor(t, w.pts, w.nrm, w.wts, w.k, w.eps, opts)
+        pkg.fmmlu_free(t)
     torch.cuda.synchronize()
-    st = pkg.fmmlu_stats(h)
+    stats = pkg.fmmlu_stats(h)
     pkg.fmmlu_free(h)
-    pkg.fmmlu_free(t)
-    return {"workload": args.workload, "n": s.n, "precision": args.precision, "n0": st["n0"],
-            "kernels": st["kernels"]}
+    return {"workload": args.workload, "n": w.n, "precision": stats["precision"],
+            "proxy_rule": rule, "n_proxy": npx, "n0": stats["n0"],
+            "kernels": stats["kernels"]}
 
 
 def scaling(args) -> list:
@@ -792,6 +811,8 @@ def main():
     ap.add_argument("--factor-once", action="store_true",
                     help="one profiled tree + factor of the workload (ncu captures); "
                          "prints the per-kernel algorithmic flops/bytes")
+    ap.add_argument("--step-once", action="store_true",
+                    help="one profiled step (tree, factor, solve, adjoint) of the workload")
     ap.add_argument("--n", type=int, default=None,
                     help="with --factor-once: the same surface family at n points")
     ap.add_argument("--scaling", action="store_true",
@@ -804,7 +825,7 @@ def main():
     args.n_proxy = args.n_proxy or npx
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.factor_once:
+    if args.factor_once or args.step_once:
         print(json.dumps(factor_once(args)))
         return
     if args.scaling:

@@ -25,6 +25,7 @@
 #include <set>
 #include <sstream>
 #include <stdexcept>
+#include <thread>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -56,10 +57,38 @@ struct Error : std::runtime_error {
 constexpr uint32_t kTreeMagic = 0x54554d46u;    // "FMUT"
 constexpr uint32_t kHandleMagic = 0x48554d46u;  // "FMUH"
 
+// Host-side time of a factorization (stats "host_ms"): device allocation and
+// release, waits for the stream, level set-up; accumulated on the thread
+// that runs the factorization.
+struct HostTimes {
+  double alloc = 0, release = 0, wait = 0, make_level = 0, plan = 0, setup = 0;
+  int64_t allocs = 0;
+};
+thread_local HostTimes* g_ht = nullptr;
+
+struct HostTimer {
+  double* acc;
+  std::chrono::steady_clock::time_point t0;
+  explicit HostTimer(double HostTimes::*m)
+      : acc(g_ht ? &(g_ht->*m) : nullptr), t0(std::chrono::steady_clock::now()) {}
+  ~HostTimer() {
+    if (acc)
+      *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                  .count();
+  }
+};
+
+inline void stream_wait(cudaStream_t st) {
+  HostTimer t(&HostTimes::wait);
+  CK(cudaStreamSynchronize(st));
+}
+
 template <typename T>
 T* dalloc(size_t count) {
   if (count == 0) count = 1;
   void* p = nullptr;
+  HostTimer t(&HostTimes::alloc);
+  if (g_ht) ++g_ht->allocs;
   CK(cudaMalloc(&p, count * sizeof(T)));
   return static_cast<T*>(p);
 }
@@ -75,7 +104,7 @@ template <typename T>
 std::vector<T> ddownload(const T* p, size_t count, cudaStream_t st) {
   std::vector<T> v(count);
   if (count) CK(cudaMemcpyAsync(v.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  stream_wait(st);
   return v;
 }
 
@@ -95,10 +124,51 @@ struct DevPool {
     return p;
   }
   void release() {
+    HostTimer t(&HostTimes::release);
     for (auto it = ptrs.rbegin(); it != ptrs.rend(); ++it) cudaFree(*it);
     ptrs.clear();
   }
   ~DevPool() { release(); }
+};
+
+// Scratch buffers reused from one level to the next: the k-th request of a
+// level gets the k-th slot, grown (freed and allocated larger) only when it
+// is too small, so a factorization allocates each scratch buffer a few times
+// instead of once per level. Uploads are stream-ordered after the work that
+// read the slot's previous contents; growing frees through cudaFree, which
+// waits for the device.
+struct ScratchPool {
+  std::vector<std::pair<void*, size_t>> slots;
+  size_t next = 0;
+  void reset() { next = 0; }
+  template <typename T>
+  T* get(size_t count) {
+    const size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+    if (next == slots.size()) slots.push_back({nullptr, 0});
+    auto& sl = slots[next++];
+    if (sl.second < bytes) {
+      if (sl.first) {
+        HostTimer t(&HostTimes::release);
+        cudaFree(sl.first);
+      }
+      sl.first = nullptr;
+      sl.second = 0;
+      sl.first = dalloc<unsigned char>(bytes);
+      sl.second = bytes;
+    }
+    return static_cast<T*>(sl.first);
+  }
+  template <typename T>
+  T* up(const std::vector<T>& v, cudaStream_t st) {
+    T* p = get<T>(v.size());
+    if (!v.empty())
+      CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return p;
+  }
+  ~ScratchPool() {
+    for (auto& sl : slots)
+      if (sl.first) cudaFree(sl.first);
+  }
 };
 
 inline void cudaFreeHost_void(BoxRun* p) { if (p) cudaFreeHost(p); }
@@ -117,10 +187,13 @@ struct UnitBuf {
   void upload(const std::vector<TcUnit>& u, cudaStream_t st) {
     if (u.empty()) return;
     if (!copied) CK(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
-    if (pending) CK(cudaEventSynchronize(copied));
+    if (pending) {
+      HostTimer t(&HostTimes::wait);
+      CK(cudaEventSynchronize(copied));
+    }
     pending = false;
     if (u.size() > cap) {
-      CK(cudaStreamSynchronize(st));
+      stream_wait(st);
       release_buffers();
       cap = std::max(u.size(), (size_t)4096);
       CK(cudaMallocHost(&h, cap * sizeof(TcUnit)));
@@ -289,15 +362,67 @@ namespace {
 // level state
 // ---------------------------------------------------------------------------
 
+// tree id -> current index (-1: not current), a flat table over all boxes
+struct CurIndex {
+  std::vector<int> v;
+  void reset(size_t nboxes) { v.assign(nboxes, -1); }
+  int find(int id) const { return id >= 0 && (size_t)id < v.size() ? v[id] : -1; }
+  int at(int id) const {
+    const int c = find(id);
+    if (c < 0) throw Error(FMMLU_ERR_CUDA, "internal: box not current");
+    return c;
+  }
+};
+
+// Run f(begin, end) over [0, n) on up to 16 host threads (contiguous
+// ranges, so per-range results concatenate in order). f must not throw.
+template <class F>
+void parallel_for(int64_t n, F f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>(std::min<unsigned>(16u, hw), std::max<int64_t>(1, n / 2048));
+  if (nt <= 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b < e) th.emplace_back([=, &f] { f(b, e); });
+  }
+  for (auto& x : th) x.join();
+}
+
+// The Schur blocks of one level: for every current box x the sorted list of
+// the boxes y that have a block (x, y) with x's rows, and each block's offset
+// in the pool (blocks are laid out x-major, then by y).
+struct PairCSR {
+  std::vector<int64_t> start;   // nc + 1
+  std::vector<int> ys;
+  std::vector<int64_t> off;
+  int64_t find(int x, int y) const {
+    if (x < 0 || (size_t)x + 1 >= start.size()) return -1;
+    const int* b = ys.data() + start[x];
+    const int* e = ys.data() + start[x + 1];
+    const int* it = std::lower_bound(b, e, y);
+    return (it != e && *it == y) ? off[it - ys.data()] : -1;
+  }
+  int64_t at(int x, int y) const {
+    const int64_t v = find(x, y);
+    if (v < 0) throw Error(FMMLU_ERR_CUDA, "internal: missing Schur pair");
+    return v;
+  }
+  size_t size() const { return ys.size(); }
+};
+
 struct LevelState {
   int level = 0;
   std::vector<int> cur;                    // tree ids of current boxes
-  std::unordered_map<int, int> cidx;       // tree id -> current index
+  CurIndex cidx;                           // tree id -> current index
   std::vector<int> a0, off;                // per current box
   std::vector<int> act_dof;                // level-start DOFs (concatenated)
   std::vector<int> cur_n, act_pos;         // after processing (host copies)
-  std::unordered_map<uint64_t, int64_t> pair;   // (cur x, cur y) -> pool offset
-  std::vector<std::pair<int, int>> pair_list;
+  PairCSR pair;                            // (cur x, cur y) -> pool offset
   DevPool mem;
   int *d_cur_n = nullptr, *d_cur_off = nullptr, *d_cur_a0 = nullptr;
   int *d_act_dof = nullptr, *d_act_pos = nullptr;
@@ -316,7 +441,8 @@ std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const Level
   L->level = level;
   L->cur = current_boxes(T, level);
   int nc = (int)L->cur.size();
-  for (int c = 0; c < nc; ++c) L->cidx[L->cur[c]] = c;
+  L->cidx.reset(T.boxes.size());
+  for (int c = 0; c < nc; ++c) L->cidx.v[L->cur[c]] = c;
   L->a0.resize(nc);
   L->off.resize(nc);
   for (int c = 0; c < nc; ++c) {
@@ -325,9 +451,7 @@ std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const Level
     L->off[c] = (int)L->act_dof.size();
     if (b.level == level && !b.leaf()) {
       for (int ch : b.kids) {
-        auto it = prev->cidx.find(ch);
-        if (it == prev->cidx.end()) throw Error(FMMLU_ERR_CUDA, "internal: child not current");
-        prev->active_dofs(it->second, L->act_dof);
+        prev->active_dofs(prev->cidx.at(ch), L->act_dof);
       }
     } else {
       for (int64_t p = b.start; p < b.end; ++p) L->act_dof.push_back((int)p);
@@ -338,35 +462,96 @@ std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const Level
   L->act_pos.resize(L->act_dof.size());
   for (int c = 0; c < nc; ++c)
     for (int i = 0; i < L->a0[c]; ++i) L->act_pos[L->off[c] + i] = i;
-  // pair set: images of the previous pairs, plus closed-neighbourhood pairs
-  auto add = [&](int x, int y) {
-    uint64_t key = pkey(x, y);
-    if (L->pair.count(key)) return;
-    L->pair[key] = -1;
-    L->pair_list.push_back({x, y});
-  };
-  auto image = [&](int prev_c) -> int {
-    int X = prev->cur[prev_c];
-    const HBox& b = T.boxes[X];
-    int Y = b.level == level + 1 ? b.parent : X;
-    return L->cidx.at(Y);
-  };
-  if (prev)
-    for (auto& pr : prev->pair_list) add(image(pr.first), image(pr.second));
-  if (lists) {
-    for (size_t r = 0; r < lists->boxes.size(); ++r) {
-      std::vector<int> cn = {L->cidx.at(lists->boxes[r])};
-      for (int j = lists->nbeg[r]; j < lists->nbeg[r] + lists->ncnt[r]; ++j)
-        cn.push_back(L->cidx.at(lists->nlist[j]));
-      for (int x : cn)
-        for (int y : cn) add(x, y);
+  // pair set: images of the previous pairs, plus closed-neighbourhood pairs.
+  // Built per row box x without hashing: the candidate columns of x are the
+  // images of the previous pairs whose row maps to x and the closed
+  // neighbourhoods {B} u N(B) that contain x; a per-thread stamp array drops
+  // duplicates, and every row is sorted.
+  std::vector<int> img;   // previous current box -> its image at this level
+  if (prev) {
+    img.resize(prev->cur.size());
+    for (size_t c = 0; c < prev->cur.size(); ++c) {
+      const HBox& b = T.boxes[prev->cur[c]];
+      img[c] = L->cidx.at(b.level == level + 1 ? b.parent : prev->cur[c]);
     }
   }
-  int64_t tot = 0;
-  for (auto& pr : L->pair_list) {
-    L->pair[pkey(pr.first, pr.second)] = tot;
-    tot += (int64_t)L->a0[pr.first] * L->a0[pr.second];
+  // previous pairs grouped by the image of their row: rows of prev map to x
+  std::vector<int64_t> pstart(nc + 1, 0);
+  std::vector<int> prow_src;   // previous rows, grouped by image
+  if (prev) {
+    for (size_t c = 0; c < prev->cur.size(); ++c) ++pstart[img[c] + 1];
+    for (int c = 0; c < nc; ++c) pstart[c + 1] += pstart[c];
+    prow_src.resize(prev->cur.size());
+    std::vector<int64_t> fill(pstart.begin(), pstart.end() - 1);
+    for (size_t c = 0; c < prev->cur.size(); ++c) prow_src[fill[img[c]]++] = (int)c;
   }
+  // closed neighbourhoods, and for every x the level boxes whose
+  // neighbourhood holds it
+  std::vector<int64_t> cnb;   // per level box: start into cn
+  std::vector<int> cn;
+  std::vector<int64_t> istart(nc + 1, 0);
+  std::vector<int> inv;
+  if (lists) {
+    const size_t nbx = lists->boxes.size();
+    cnb.resize(nbx + 1, 0);
+    for (size_t r = 0; r < nbx; ++r) {
+      cnb[r] = (int64_t)cn.size();
+      cn.push_back(L->cidx.at(lists->boxes[r]));
+      for (int j = lists->nbeg[r]; j < lists->nbeg[r] + lists->ncnt[r]; ++j)
+        cn.push_back(L->cidx.at(lists->nlist[j]));
+    }
+    cnb[nbx] = (int64_t)cn.size();
+    for (int x : cn) ++istart[x + 1];
+    for (int c = 0; c < nc; ++c) istart[c + 1] += istart[c];
+    inv.resize(cn.size());
+    std::vector<int64_t> fill(istart.begin(), istart.end() - 1);
+    for (size_t r = 0; r < nbx; ++r)
+      for (int64_t q = cnb[r]; q < cnb[r + 1]; ++q) inv[fill[cn[q]]++] = (int)r;
+  }
+  // rows, in parallel over contiguous ranges of x
+  std::vector<int64_t> rcount(nc, 0);
+  std::vector<std::vector<int>> parts;
+  std::mutex pmu;
+  std::vector<std::pair<int64_t, int>> part_of;   // range begin -> part index
+  parallel_for(nc, [&](int64_t x0, int64_t x1) {
+    std::vector<int> stamp(nc, -1), row, out;
+    for (int64_t x = x0; x < x1; ++x) {
+      row.clear();
+      auto take = [&](int y) {
+        if (stamp[y] != (int)x) { stamp[y] = (int)x; row.push_back(y); }
+      };
+      if (prev)
+        for (int64_t q = pstart[x]; q < pstart[x + 1]; ++q) {
+          const int xp = prow_src[q];
+          const PairCSR& P = prev->pair;
+          for (int64_t e = P.start[xp]; e < P.start[xp + 1]; ++e) take(img[P.ys[e]]);
+        }
+      for (int64_t q = istart[x]; q < istart[x + 1]; ++q) {
+        const int r = inv[q];
+        for (int64_t e = cnb[r]; e < cnb[r + 1]; ++e) take(cn[e]);
+      }
+      std::sort(row.begin(), row.end());
+      rcount[x] = (int64_t)row.size();
+      out.insert(out.end(), row.begin(), row.end());
+    }
+    std::lock_guard<std::mutex> lk(pmu);
+    part_of.push_back({x0, (int)parts.size()});
+    parts.push_back(std::move(out));
+  });
+  std::sort(part_of.begin(), part_of.end());
+  PairCSR& P = L->pair;
+  P.start.assign(nc + 1, 0);
+  for (int x = 0; x < nc; ++x) P.start[x + 1] = P.start[x] + rcount[x];
+  P.ys.reserve((size_t)P.start[nc]);
+  for (auto& po : part_of) P.ys.insert(P.ys.end(), parts[po.second].begin(), parts[po.second].end());
+  parts.clear();
+  P.off.resize(P.ys.size());
+  int64_t tot = 0;
+  for (int x = 0; x < nc; ++x)
+    for (int64_t e = P.start[x]; e < P.start[x + 1]; ++e) {
+      P.off[e] = tot;
+      tot += (int64_t)L->a0[x] * L->a0[P.ys[e]];
+    }
   L->pool_size = tot;
   L->d_pool = L->mem.get<double2>((size_t)tot);
   if (tot) CK(cudaMemsetAsync(L->d_pool, 0, (size_t)tot * sizeof(double2), st));
@@ -376,39 +561,56 @@ std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const Level
   L->d_act_dof = L->mem.up(L->act_dof, st);
   L->d_act_pos = L->mem.up(L->act_pos, st);
   // gather the previous Schur blocks into the new pool
-  if (prev && !prev->pair_list.empty()) {
-    std::vector<MergeItem> items;
+  if (prev && prev->pair.size() > 0) {
     std::vector<int> suboff(prev->cur.size(), 0);   // offset of prev box inside its image
     {
-      std::unordered_map<int, int> run;   // image -> running offset (children in order)
+      std::vector<int> run(nc, 0);   // image -> running offset (children in order)
       for (size_t c = 0; c < prev->cur.size(); ++c) {
-        int X = prev->cur[c];
-        const HBox& b = T.boxes[X];
+        const HBox& b = T.boxes[prev->cur[c]];
         if (b.level == level + 1) {
           // children of one parent are consecutive in current order (by start)
-          int img = L->cidx.at(b.parent);
-          int& o = run[img];
+          int& o = run[img[c]];
           suboff[c] = o;
           o += prev->cur_n[c];
         }
       }
     }
-    for (auto& pr : prev->pair_list) {
-      int x = pr.first, y = pr.second;
-      int X = image(x), Y = image(y);
-      MergeItem it;
-      it.src = prev->d_pool + prev->pair.at(pkey(x, y));
-      it.dst = L->d_pool + L->pair.at(pkey(X, Y));
-      it.ld_src = prev->a0[x];
-      it.ld_dst = L->a0[X];
-      it.off_i = suboff[x];
-      it.off_j = suboff[y];
-      it.ni = prev->cur_n[x];
-      it.nj = prev->cur_n[y];
-      it.pos_i = prev->d_act_pos + prev->off[x];
-      it.pos_j = prev->d_act_pos + prev->off[y];
-      if (it.ni > 0 && it.nj > 0) items.push_back(it);
-    }
+    const PairCSR& Q = prev->pair;
+    const int npc = (int)prev->cur.size();
+    std::vector<std::vector<MergeItem>> iparts;
+    std::vector<std::pair<int64_t, int>> ipart_of;
+    bool missing = false;
+    parallel_for(npc, [&](int64_t x0, int64_t x1) {
+      std::vector<MergeItem> items;
+      bool miss = false;
+      for (int64_t x = x0; x < x1; ++x)
+        for (int64_t e = Q.start[x]; e < Q.start[x + 1]; ++e) {
+          const int y = Q.ys[e];
+          const int X = img[x], Y = img[y];
+          MergeItem it;
+          const int64_t dst = L->pair.find(X, Y);
+          if (dst < 0) { miss = true; continue; }
+          it.src = prev->d_pool + Q.off[e];
+          it.dst = L->d_pool + dst;
+          it.ld_src = prev->a0[x];
+          it.ld_dst = L->a0[X];
+          it.off_i = suboff[x];
+          it.off_j = suboff[y];
+          it.ni = prev->cur_n[x];
+          it.nj = prev->cur_n[y];
+          it.pos_i = prev->d_act_pos + prev->off[x];
+          it.pos_j = prev->d_act_pos + prev->off[y];
+          if (it.ni > 0 && it.nj > 0) items.push_back(it);
+        }
+      std::lock_guard<std::mutex> lk(pmu);
+      missing = missing || miss;
+      ipart_of.push_back({x0, (int)iparts.size()});
+      iparts.push_back(std::move(items));
+    });
+    if (missing) throw Error(FMMLU_ERR_CUDA, "internal: missing Schur pair");
+    std::sort(ipart_of.begin(), ipart_of.end());
+    std::vector<MergeItem> items;
+    for (auto& po : ipart_of) items.insert(items.end(), iparts[po.second].begin(), iparts[po.second].end());
     MergeItem* d_items = L->mem.up(items, st);
     launch_merge(d_items, (int)items.size(), 0, 0, st);
     CK(cudaGetLastError());
@@ -619,9 +821,16 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   H->autotune = opt.solve_chunk == 0 ? opt.autotune : 0;
   H->tune_cache = opt.autotune_cache ? opt.autotune_cache : "";
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
+  HostTimes ht;
+  struct HtScope {
+    HostTimes* saved;
+    explicit HtScope(HostTimes* p) : saved(g_ht) { g_ht = p; }
+    ~HtScope() { g_ht = saved; }
+  } ht_scope(&ht);
   Timer total_timer;
   DevPool work;   // freed at the end of the factorization
   UnitBuf gram_units, elim_units;   // launch lists of the tcgen05 path
+  ScratchPool level_scratch;
   H->d_perm = H->mem.get<int>((size_t)n);
   CK(cudaMemcpyAsync(H->d_perm, tree->d_perm, n * sizeof(int), cudaMemcpyDeviceToDevice, st));
   double* soa = work.get<double>((size_t)n * 8);
@@ -642,8 +851,13 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   for (int lev = T.nlevels - 1; lev >= 2; --lev) {
     Timer lt;
     const HLevel& HL = T.levels.at(lev);
-    auto L = make_level(T, lev, prev.get(), &HL, st);
-    CK(cudaStreamSynchronize(st));   // the merge has read the previous level
+    std::unique_ptr<LevelState> L;
+    {
+      HostTimer mt(&HostTimes::make_level);
+      L = make_level(T, lev, prev.get(), &HL, st);
+    }
+    stream_wait(st);   // the merge has read the previous level
+    const auto setup0 = std::chrono::steady_clock::now();
     prev.reset();
     // stop rule: any level box with active far DOFs?
     const int nb = (int)HL.boxes.size();
@@ -666,6 +880,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     std::vector<BoxDesc> desc(nb);
     std::vector<int> nlist, qlist;
     std::vector<int64_t> pairtab, qpair;
+    int64_t ptab_size = 0, qpair_size = 0;
     std::vector<int> seg_start;
     int64_t arena = 0, iarena = 0;
     const double hreal = T.side / (double)(1 << lev);
@@ -698,22 +913,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       d.cx = T.corner[0] + ((double)hb.cx + 0.5) * hreal;
       d.cy = T.corner[1] + ((double)hb.cy + 0.5) * hreal;
       d.cz = T.corner[2] + ((double)hb.cz + 0.5) * hreal;
-      std::vector<int> cn = {d.cur};
-      for (int j = 0; j < d.ncnt; ++j) cn.push_back(nlist[d.nbeg + j]);
-      d.pairtab = (int64_t)pairtab.size();
-      for (int x : cn)
-        for (int y : cn) {
-          auto it = L->pair.find(pkey(x, y));
-          pairtab.push_back(it == L->pair.end() ? -1 : it->second);
-        }
-      d.qpair = (int64_t)qpair.size();
-      for (int j = 0; j < d.qcnt; ++j) {
-        int c = qlist[d.qbeg + j];
-        auto i1 = L->pair.find(pkey(c, d.cur));
-        auto i2 = L->pair.find(pkey(d.cur, c));
-        qpair.push_back(i1 == L->pair.end() ? -1 : i1->second);
-        qpair.push_back(i2 == L->pair.end() ? -1 : i2->second);
-      }
+      // block offsets are looked up below, in parallel over the boxes
+      d.pairtab = ptab_size;
+      ptab_size += (int64_t)(d.ncnt + 1) * (d.ncnt + 1);
+      d.qpair = qpair_size;
+      qpair_size += 2 * (int64_t)d.qcnt;
       int64_t a = d.a, nm = d.nmax;
       d.G1_off = arena; arena += a * (a + nm);
       d.G3_off = arena; arena += (a + nm) * a;
@@ -723,6 +927,27 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (e == 0 || HL.colour[HL.order[e - 1]] != HL.colour[r]) seg_start.push_back(e);
     }
     seg_start.push_back(nb);
+    // pool offsets of the blocks between the boxes of each closed
+    // neighbourhood {B} u N(B), and of the blocks (q, B), (B, q) for q in Q(B)
+    pairtab.resize((size_t)ptab_size);
+    qpair.resize((size_t)qpair_size);
+    parallel_for(nb, [&](int64_t e0, int64_t e1) {
+      std::vector<int> cn;
+      for (int64_t e = e0; e < e1; ++e) {
+        const BoxDesc& d = desc[e];
+        cn.assign(1, d.cur);
+        for (int j = 0; j < d.ncnt; ++j) cn.push_back(nlist[d.nbeg + j]);
+        int64_t o = d.pairtab;
+        for (int x : cn)
+          for (int y : cn) pairtab[o++] = L->pair.find(x, y);
+        o = d.qpair;
+        for (int j = 0; j < d.qcnt; ++j) {
+          const int c = qlist[d.qbeg + j];
+          qpair[o++] = L->pair.find(c, d.cur);
+          qpair[o++] = L->pair.find(d.cur, c);
+        }
+      }
+    });
     // per-colour scratch offsets (reset at each colour start)
     int64_t rows_max = 0, M_max = 0, W_max = 0;
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
@@ -737,7 +962,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       M_max = std::max(M_max, mo);
       W_max = std::max(W_max, wo);
     }
-    DevPool lw;   // level scratch
+    ScratchPool& lw = level_scratch;   // level scratch, reused across levels
+    lw.reset();
     double2* d_arena = H->mem.get<double2>((size_t)arena);
     int* d_iarena = H->mem.get<int>((size_t)iarena);
     H->arena_bytes += arena * 16 + iarena * 4;
@@ -1012,6 +1238,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     CpqrPart* d_parts = lw.up(parts, st);
     unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
     unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
+    ht.setup += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                          setup0).count();
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
       int amax = 1, mmax = 1, nmaxm = 0;
@@ -1065,7 +1293,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (use_tc) {
         CK(cudaMemcpyAsync(h_run + b0, d_run + b0, cnt * sizeof(BoxRun), cudaMemcpyDeviceToHost,
                            st));
-        CK(cudaStreamSynchronize(st));
+        stream_wait(st);
+        HostTimer pt(&HostTimes::plan);
         std::vector<TcBoxSize> bs(cnt);
         for (int e = 0; e < cnt; ++e) {
           const BoxRun& q = h_run[b0 + e];
@@ -1201,7 +1430,9 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           H->prof.add_work("cpqr", qr, m * a * csz);
         }
         if (rr.r == 0) continue;
-        H->prof.add_work("assemble_elim", 0, 2.0 * a * (a + n_) * 16.0);
+        // G1 and G3 entries come in pairs from one kernel evaluation
+        H->prof.add_work("assemble_elim", kKevalFlops * 2.0 * a * (a + n_),
+                         2.0 * a * (a + n_) * 16.0);
         // complex products: 8 fp64 flops per multiply-add on the FMA path; on
         // the tensor-core path (inner dimension >= kOzInnerMin) 28 digit pairs
         // x 4 real bf16 products x 2 flops, and the digit split of the operands
@@ -1320,8 +1551,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   if (prev && prev->level == root_level) {
     R = std::move(prev);
   } else {
-    R = make_level(T, root_level, prev.get(), nullptr, st);
-    CK(cudaStreamSynchronize(st));
+    {
+      HostTimer mt(&HostTimes::make_level);
+      R = make_level(T, root_level, prev.get(), nullptr, st);
+    }
+    stream_wait(st);
     prev.reset();
   }
   int n0 = (int)R->total();
@@ -1332,7 +1566,9 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     for (int c = 0; c < nc; ++c)
       for (int i = 0; i < R->a0[c]; ++i) { owner[R->off[c] + i] = c; pos[R->off[c] + i] = i; }
     std::vector<int64_t> pairoff((size_t)nc * nc, -1);
-    for (auto& kv : R->pair) pairoff[(size_t)(kv.first >> 32) * nc + (uint32_t)kv.first] = kv.second;
+    for (int x = 0; x < nc; ++x)
+      for (int64_t e = R->pair.start[x]; e < R->pair.start[x + 1]; ++e)
+        pairoff[(size_t)x * nc + R->pair.ys[e]] = R->pair.off[e];
     DevPool rw;
     int* d_owner = rw.up(owner, st);
     int* d_pos = rw.up(pos, st);
@@ -1380,7 +1616,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     for (const SweepSeg& sg : H->sseg) { mix(sg.b0); mix(sg.nb); }
     H->shape_key = hs;
   }
-  CK(cudaStreamSynchronize(st));
+  stream_wait(st);
   double tot_ms = total_timer.ms();
   if (opt.verbose)
     std::fprintf(stderr, "[fmmlu] root level %d n0 %d %.1f ms; factor %.1f ms; m_f %.1f MB\n",
@@ -1388,7 +1624,10 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   js << "], \"root_level\": " << root_level << ", \"n0\": " << n0 << ", \"root_ms\": " << root_ms
      << ", \"factor_ms\": " << tot_ms << ", \"factor_bytes\": " << H->factor_entries * 16
      << ", \"arena_bytes\": " << H->arena_bytes << ", \"eliminated_boxes\": " << H->sboxes.size()
-     << ", \"colour_segments\": " << H->sseg.size() << "}";
+     << ", \"colour_segments\": " << H->sseg.size() << ", \"host_ms\": {\"alloc\": " << ht.alloc
+     << ", \"allocs\": " << ht.allocs << ", \"release\": " << ht.release
+     << ", \"wait\": " << ht.wait << ", \"make_level\": " << ht.make_level
+     << ", \"plan\": " << ht.plan << ", \"level_setup\": " << ht.setup << "}}";
   H->stats = js.str();
 }
 
@@ -1801,7 +2040,7 @@ int fmmlu_build_tree(const double* points, int64_t n, const fmmlu_opts* opts, vo
     auto t = std::make_unique<fmmlu_tree>();
     t->opts = o;
     std::string msg;
-    if (int rc = gpu_build_tree(points, n, o.leaf_size, t->T, &t->d_perm, msg, st))
+    if (int rc = gpu_build_tree(points, n, o.leaf_size, t->T, &t->d_perm, msg, o.verbose, st))
       throw Error(rc, "tree: " + msg);
     *out = t.release();
   });

@@ -25,12 +25,15 @@
 //    first point: N(B) = those touching B, Q(B) = those at max-norm gap in
 //    (0, h_l]. Two passes (counts, then lists at scanned offsets).
 // 6. Colours, greedy in Morton order over the conflict relation gap <= h_l or
-//    a shared coarser leaf in the near lists: one CTA per level walks the
-//    level's boxes in order (each box's conflict colours are gathered into a
-//    shared bit set by all threads, the smallest free colour taken).
+//    a shared coarser leaf in the near lists: every box's earlier
+//    conflicting boxes are listed in parallel, then one warp per level walks
+//    the level's boxes in order and gives each the smallest colour none of
+//    its listed boxes has.
 // The host downloads the finished arrays into its description of the tree.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
@@ -586,53 +589,106 @@ __device__ __forceinline__ int lower_key(const unsigned long long* __restrict__ 
   return a;
 }
 
-// block = one warp; level = lev0 + blockIdx.x with boxes [lstart[level],
-// lstart[level + 1]); colours go to col (by box id) and the count to ncol
-__global__ void __launch_bounds__(32) k_colour(const DBoxes B, const DLists Ls, const int* lstart,
-                                               int lev0, int t0, int nu_total, int smem_boxes,
-                                               int* col, int* ncol, int* fail) {
-  extern __shared__ unsigned short scol[];   // colours of this level (when they fit)
-  __shared__ unsigned mask[kMaxColours / 32];
+// Earlier conflicting boxes of every level box (one thread per box): the
+// same-level boxes at gap <= h and the boxes sharing a coarser near leaf,
+// each with an index below the box's own. fill = 0 counts, 1 writes.
+__global__ void k_conflicts(const DBoxes B, const DLists Ls, int t0, int nbox, int nu_total,
+                            int* ccnt, const int* coff, int* conf, int fill) {
+  const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nbox) return;
+  const int r = t - t0;
+  const int level = B.lvl[t];
+  int c = 0;
+  const int o0 = fill ? coff[r] : 0;
+  for (int q = 0; q < Ls.scnt[r]; ++q) {
+    const int o = Ls.slist[Ls.soff[r] + q];
+    if (o < t) {
+      if (fill) conf[o0 + c] = o;
+      ++c;
+    }
+  }
+  for (int q = 0; q < Ls.ncnt[r]; ++q) {
+    const int cbox = Ls.nlist[Ls.noff[r] + q];
+    if (B.lvl[cbox] >= level) continue;
+    const unsigned long long key = ((unsigned long long)level << 32) | (unsigned)cbox;
+    for (int u = lower_key(Ls.ukey, 0, nu_total, key); u < nu_total && Ls.ukey[u] == key; ++u) {
+      const int o = Ls.uval[u];
+      if (o < t) {
+        if (fill) conf[o0 + c] = o;
+        ++c;
+      }
+    }
+  }
+  if (!fill) ccnt[r] = c;
+}
+
+// Greedy colours in Morton order: one warp per level (level = lev0 +
+// blockIdx.x, boxes [lstart[level], lstart[level + 1])) walks its boxes in
+// order; a box takes the smallest colour that none of its earlier
+// conflicting boxes has. Colours below 64 are gathered in registers and
+// or-reduced over the warp, larger ones in a shared bit set. The next box's
+// first 64 conflicts are loaded while the current box is coloured. Colours
+// live in shared memory when the level fits (smem_boxes), else in col.
+__global__ void __launch_bounds__(32) k_colour(const int* __restrict__ ccnt,
+                                               const int* __restrict__ coff,
+                                               const int* __restrict__ conf, const int* lstart,
+                                               int lev0, int t0, int smem_boxes, int* col,
+                                               int* ncol, int* fail) {
+  extern __shared__ unsigned short scol[];
+  __shared__ unsigned mask_hi[kMaxColours / 32];
   const int level = lev0 + blockIdx.x;
   const int b0 = lstart[level], b1 = lstart[level + 1];
   const int nb = b1 - b0;
   const int lane = threadIdx.x;
   const bool in_smem = nb <= smem_boxes;
-  for (int w = lane; w < kMaxColours / 32; w += 32) mask[w] = 0;
+  for (int w = lane; w < kMaxColours / 32; w += 32) mask_hi[w] = 0;
   __syncwarp();
+  auto colour_of = [&](int o) -> int {
+    return in_smem ? (int)scol[o - b0] : ((volatile int*)col)[o];
+  };
+  auto fetch = [&](int rb, int& cnt, int& e0, int& e1) {
+    cnt = 0; e0 = -1; e1 = -1;
+    if (rb >= b1) return;
+    const int r = rb - t0;
+    cnt = ccnt[r];
+    const int off = coff[r];
+    if (lane < cnt) e0 = conf[off + lane];
+    if (lane + 32 < cnt) e1 = conf[off + 32 + lane];
+  };
+  int cnt, e0, e1;
+  fetch(b0, cnt, e0, e1);
   int maxc = -1;
   for (int rb = b0; rb < b1; ++rb) {
-    const int r = rb - t0;
-    // same-level conflicts
-    const int so = Ls.soff[r], sc = Ls.scnt[r];
-    for (int q = lane; q < sc; q += 32) {
-      const int o = Ls.slist[so + q];
-      if (o < rb) {
-        const int c = in_smem ? scol[o - b0] : ((volatile int*)col)[o];
-        atomicOr(&mask[c >> 5], 1u << (c & 31));
-      }
+    int ncnt, n0, n1;
+    fetch(rb + 1, ncnt, n0, n1);   // independent of the colours: overlaps
+    unsigned long long bits = 0;
+    bool high = false;
+    auto take = [&](int o) {
+      const int c = colour_of(o);
+      if (c < 64) bits |= 1ull << c;
+      else { atomicOr(&mask_hi[c >> 5], 1u << (c & 31)); high = true; }
+    };
+    if (e0 >= 0) take(e0);
+    if (e1 >= 0) take(e1);
+    if (cnt > 64) {
+      const int off = coff[rb - t0];
+      for (int q = 64 + lane; q < cnt; q += 32) take(conf[off + q]);
     }
-    // boxes sharing a coarser near leaf
-    const int no = Ls.noff[r], nn = Ls.ncnt[r];
-    for (int q = lane; q < nn; q += 32) {
-      const int cbox = Ls.nlist[no + q];
-      if (B.lvl[cbox] >= level) continue;
-      const unsigned long long key = ((unsigned long long)level << 32) | (unsigned)cbox;
-      for (int u = lower_key(Ls.ukey, 0, nu_total, key); u < nu_total && Ls.ukey[u] == key; ++u) {
-        const int o = Ls.uval[u];
-        if (o < rb) {
-          const int c = in_smem ? scol[o - b0] : ((volatile int*)col)[o];
-          atomicOr(&mask[c >> 5], 1u << (c & 31));
-        }
-      }
-    }
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)bits);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(bits >> 32));
+    const bool any_high = __any_sync(0xffffffffu, high);
     __syncwarp();
-    // smallest free colour: lowest word with a zero bit
-    const unsigned wv = mask[lane];
-    const unsigned full = __ballot_sync(0xffffffffu, wv != 0xffffffffu);
-    const int wfree = full ? __ffs(full) - 1 : -1;
-    const unsigned wsel = __shfl_sync(0xffffffffu, wv, wfree < 0 ? 0 : wfree);
-    const int c = wfree < 0 ? kMaxColours : wfree * 32 + (__ffs(~wsel) - 1);
+    int c;
+    if (lo != 0xffffffffu) c = __ffs(~lo) - 1;
+    else if (hi != 0xffffffffu) c = 32 + __ffs(~hi) - 1;
+    else {
+      // every colour below 64 is taken: the shared set holds the rest
+      const unsigned wv = lane >= 2 ? mask_hi[lane] : 0xffffffffu;
+      const unsigned free_w = __ballot_sync(0xffffffffu, wv != 0xffffffffu);
+      const int wf = free_w ? __ffs(free_w) - 1 : -1;
+      const unsigned wsel = __shfl_sync(0xffffffffu, wv, wf < 0 ? 0 : wf);
+      c = wf < 0 ? kMaxColours : wf * 32 + (__ffs(~wsel) - 1);
+    }
     if (lane == 0) {
       if (c >= kMaxColours) *fail = 3;
       const int cc = c >= kMaxColours ? 0 : c;
@@ -640,8 +696,11 @@ __global__ void __launch_bounds__(32) k_colour(const DBoxes B, const DLists Ls, 
       ((volatile int*)col)[rb] = cc;
     }
     maxc = max(maxc, c);
-    mask[lane] = 0;
+    if (any_high) {
+      mask_hi[lane] = 0;
+    }
     __syncwarp();
+    cnt = ncnt; e0 = n0; e1 = n1;
   }
   if (lane == 0) ncol[level] = maxc + 1;
 }
@@ -786,7 +845,15 @@ __global__ void k_root(DBoxes B, DHash H, int n, int* fail) {
 }  // namespace
 
 int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int** d_perm_out,
-                   std::string& msg, cudaStream_t st) {
+                   std::string& msg, int verbose, cudaStream_t st) {
+  const auto t_start = std::chrono::steady_clock::now();
+  std::vector<std::pair<const char*, double>> phases;
+  auto phase = [&](const char* name) {
+    if (!verbose) return;
+    TCK(cudaStreamSynchronize(st));
+    phases.push_back({name, std::chrono::duration<double, std::milli>(
+                                std::chrono::steady_clock::now() - t_start).count()});
+  };
   try {
     DMem mem;
     int* d_flags = mem.get<int>(8);   // [0] hash/fail, [1] bad point, [2] counter, [3] total
@@ -818,6 +885,7 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
     FMMLU_LAUNCH("morton", st, k_morton<<<dgrid(n, 256), 256, 0, st>>>(
                                    pts, n, T.corner[0], T.corner[1], T.corner[2], side, k0, v0));
     auto sorted = radix_sort(k0, v0, k1, v1, mem, n, 16, st);
+    phase("keys");
     const uint64_t* keys = sorted.first;
     int* d_perm = sorted.second;
     // 2. hierarchy
@@ -840,6 +908,7 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
       b1 += tot;
     }
     int nbox = b1;
+    phase("hierarchy");
     // 3. level restriction, in rounds
     for (;;) {
       TCK(cudaMemsetAsync(d_flags + 2, 0, sizeof(int), st));
@@ -854,6 +923,7 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
       nbox = down(d_flags + 2, 1, st)[0];
     }
     if (int f = down(d_flags, 1, st)[0]) throw TreeFail{-3, "tree construction overflow " + std::to_string(f)};
+    phase("balance");
     // 4. canonical ids: (level, first point)
     uint64_t* ok0 = mem.get<uint64_t>(nbox);
     uint64_t* ok1 = mem.get<uint64_t>(nbox);
@@ -875,6 +945,7 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
     for (int t = nbox - 1; t >= 0; --t) lstart[lvl[t]] = t;
     for (int l = nlevels - 1; l >= 0; --l) lstart[l] = std::min(lstart[l], lstart[l + 1]);
     T.nlevels = nlevels;
+    phase("ids");
     // 5. near / Q lists and conflicts of every box of level >= 2
     const int t0 = nlevels > 2 ? lstart[2] : nbox;
     const int nb2 = nbox - t0;
@@ -912,6 +983,7 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
                            uv1, mem, tot[3], 10, st);
       Ls.ukey = reinterpret_cast<unsigned long long*>(us.first);
       Ls.uval = us.second;
+      phase("lists");
       // 6. colours, one warp per level
       int* d_col = mem.get<int>(nbox);
       int* d_ncol = mem.get<int>(nlevels + 1);
@@ -924,10 +996,21 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
       for (int l = 2; l < nlevels; ++l) maxnb = std::max(maxnb, lstart[l + 1] - lstart[l]);
       const int smem_boxes = maxnb <= 65536 ? maxnb : 0;
       const size_t csm = 2 * (size_t)smem_boxes;
+      int* ccnt = mem.get<int>(nb2);
+      int* coff = mem.get<int>(nb2);
+      FMMLU_LAUNCH("tree_colour", st, k_conflicts<<<dgrid(nb2, 128), 128, 0, st>>>(
+                                          B, Ls, t0, nbox, tot[3], ccnt, coff, nullptr, 0));
+      TCK(cudaMemcpyAsync(coff, ccnt, sizeof(int) * (size_t)nb2, cudaMemcpyDeviceToDevice, st));
+      FMMLU_LAUNCH("tree_scan", st, k_scan_total<<<1, 1024, 0, st>>>(coff, nb2, d_flags + 2));
+      const int nconf = down(d_flags + 2, 1, st)[0];
+      int* conf = mem.get<int>(nconf);
+      FMMLU_LAUNCH("tree_colour", st, k_conflicts<<<dgrid(nb2, 128), 128, 0, st>>>(
+                                          B, Ls, t0, nbox, tot[3], ccnt, coff, conf, 1));
       TCK(cudaFuncSetAttribute(k_colour, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
       FMMLU_LAUNCH("tree_colour", st, k_colour<<<nlevels - 2, 32, csm, st>>>(
-                                          B, Ls, d_lstart, 2, t0, tot[3], smem_boxes, d_col,
+                                          ccnt, coff, conf, d_lstart, 2, t0, smem_boxes, d_col,
                                           d_ncol, d_flags));
+      phase("colours");
       col = down(d_col, nbox, st);
       ncol = down(d_ncol, nlevels + 1, st);
       h_ncnt = down(Ls.ncnt, nb2, st);
@@ -1003,6 +1086,12 @@ int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int
       std::merge(coarse.begin(), coarse.end(), leaves.begin(), leaves.end(), merged.begin(),
                  [&](int a, int b) { return T.boxes[a].start < T.boxes[b].start; });
       coarse.swap(merged);
+    }
+    phase("host description");
+    if (verbose) {
+      std::fprintf(stderr, "[fmmlu] tree: %d boxes, %d levels;", nbox, nlevels);
+      for (auto& p : phases) std::fprintf(stderr, " %s %.2f ms", p.first, p.second);
+      std::fprintf(stderr, "\n");
     }
     // the sorted permutation stays on the device for the factorization
     int* keep = mem.get<int>(n);

@@ -44,9 +44,9 @@ struct TreeHost {
 // Builds the whole tree on the GPU (tree.cu) from device points (N x 3
 // row-major) and fills T; *d_perm receives a device copy of the sorted
 // permutation (cudaFree by the caller). Returns 0 or a negative FMMLU_ERR_*
-// code with a message.
+// code with a message. verbose: phase times (cumulative ms) on stderr.
 int gpu_build_tree(const double* pts, int64_t n, int leaf_size, TreeHost& T, int** d_perm,
-                   std::string& msg, cudaStream_t st);
+                   std::string& msg, int verbose, cudaStream_t st);
 std::vector<int> current_boxes(const TreeHost& T, int level);
 
 }  // namespace fmmlu
