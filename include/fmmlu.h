@@ -149,6 +149,14 @@ typedef struct fmmlu_opts {
                                  from it (lines "key value") and appended to
                                  it, so later processes skip the timing.
                                  The string is copied by fmmlu_factor.     */
+  int solve_tc_nrhs;          /* solves with at least this many right-hand
+                                 sides run the products with the C blocks
+                                 (X_CR z in the forward sweep, X_RC x_C in
+                                 the backward one, the bulk of the sweeps'
+                                 arithmetic) on the tcgen05 tensor cores by
+                                 the exact split of schur_emulation 1 (the
+                                 operands split on every solve); fewer run
+                                 in fp64 FMA. Default 8; 0 = never.        */
   int proxy_rule;             /* number of proxy points per sphere (Sec. 5.2,
                                  proxy surface discretization):
                                  FMMLU_PROXY_FIXED (default): n_proxy on

@@ -51,6 +51,7 @@ class fmmlu_opts(ctypes.Structure):
         ("solve_graph", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("autotune_cache", ctypes.c_char_p),
+        ("solve_tc_nrhs", ctypes.c_int),
         ("proxy_rule", ctypes.c_int),
     ]
 

@@ -62,6 +62,7 @@ constexpr uint32_t kHandleMagic = 0x48554d46u;  // "FMUH"
 // that runs the factorization.
 struct HostTimes {
   double alloc = 0, release = 0, wait = 0, make_level = 0, plan = 0, setup = 0;
+  double setup_desc = 0, setup_pairs = 0, setup_plans = 0;
   int64_t allocs = 0;
 };
 thread_local HostTimes* g_ht = nullptr;
@@ -244,6 +245,7 @@ void default_opts(fmmlu_opts* o) {
   o->xrr_refine_tol = 1e-9;
   o->solve_chunk = 0;
   o->solve_graph = 1;
+  o->solve_tc_nrhs = 8;
   o->autotune = 1;
   o->autotune_cache = nullptr;
 }
@@ -266,6 +268,7 @@ fmmlu_opts checked_opts(const fmmlu_opts* in) {
   if (o.solve_chunk != 0 && (o.solve_chunk < 16 || o.solve_chunk > 4096 || o.solve_chunk % 16))
     throw Error(FMMLU_ERR_INVALID_ARG, "solve_chunk must be 0 or a multiple of 16 in [16, 4096]");
   if (o.solve_graph < 0 || o.solve_graph > 2) throw Error(FMMLU_ERR_INVALID_ARG, "bad solve_graph");
+  if (o.solve_tc_nrhs < 0) throw Error(FMMLU_ERR_INVALID_ARG, "solve_tc_nrhs must be >= 0");
   if (o.autotune < 0 || o.autotune > 1) throw Error(FMMLU_ERR_INVALID_ARG, "bad autotune");
   return o;
 }
@@ -284,6 +287,19 @@ namespace {
 
 // The chunk items of the solve sweeps for one chunk size (rows of C per CTA
 // in the forward sweep, columns in the backward one), on the device.
+// Launch lists of the C products of the sweeps on the tensor cores for one
+// (nrhs, direction): per colour the unit lists of the operand splits and the
+// product tiles, and per box the offsets of its digit slices and exponents in
+// a per-colour scratch (the C and T products of a colour reuse it in turn).
+struct TcSolvePlan {
+  DevPool mem;
+  TcUnit* d_units = nullptr;
+  TcBoxHost* d_tbC = nullptr;
+  TcBoxHost* d_tbT = nullptr;
+  std::vector<TcPlan> plC, plT;   // per colour segment
+  int64_t slice_bytes = 256, expo_ints = 64;
+};
+
 struct SolvePlan {
   int chunk = 0;
   DevPool mem;
@@ -291,6 +307,12 @@ struct SolvePlan {
   SweepItem* d_items = nullptr;
   std::vector<SweepSeg> segs;   // elimination order
   int64_t part_max = 1;         // partial sums per right-hand side (backward sweep)
+  // tensor-core products: placeholder descriptors (one per box, zero) and a
+  // status word for the generic product kernels, and the launch lists
+  BoxDesc* d_desc = nullptr;
+  BoxRun* d_run = nullptr;
+  int* d_status = nullptr;
+  std::map<std::pair<int, int>, std::shared_ptr<TcSolvePlan>> tc;   // (nrhs, adjoint)
 };
 
 // Work vectors of the solves with one (nrhs, direction, stream, chunk) and,
@@ -305,6 +327,9 @@ struct SolveCtx {
   double2 *v = nullptr, *part = nullptr, *vr = nullptr, *z = nullptr;
   int* cnt = nullptr;           // per box and right-hand side: backward chunks done
   void* rscr = nullptr;
+  std::shared_ptr<TcSolvePlan> tcp;   // C products on the tensor cores (else fp64)
+  unsigned char* tslices = nullptr;
+  int* texpo = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;
   int64_t uses = 0;
@@ -334,6 +359,7 @@ struct fmmlu_handle {
   std::vector<SweepSeg> sseg;     // their colour segments (items not yet built)
   int chunk0 = kSweepChunkDefault;
   int solve_graph = 1, autotune = 0;
+  int solve_tc_nrhs = 8;          // tensor-core C products from this many rhs (0: never)
   std::string tune_cache;
   uint64_t shape_key = 0;         // hash of the solve structure (tuning cache key)
   int n0 = 0, nb_root = 64;
@@ -781,7 +807,51 @@ std::shared_ptr<SolvePlan> make_solve_plan(const fmmlu_handle* H, int chunk, cud
   if (items.size() > (size_t)INT32_MAX) throw Error(FMMLU_ERR_LIMIT, "too many solve items");
   P->d_boxes = P->mem.up(boxes, st);
   P->d_items = P->mem.up(items, st);
+  const size_t nbx = std::max<size_t>(1, boxes.size());
+  P->d_desc = P->mem.get<BoxDesc>(nbx);
+  P->d_run = P->mem.get<BoxRun>(nbx);
+  P->d_status = P->mem.get<int>(1);
+  CK(cudaMemsetAsync(P->d_desc, 0, nbx * sizeof(BoxDesc), st));
+  CK(cudaMemsetAsync(P->d_run, 0, nbx * sizeof(BoxRun), st));
+  CK(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
   return P;
+}
+
+// Launch lists of the tensor-core C products of plan P for nrhs right-hand
+// sides in one direction (the adjoint products read the other block,
+// transposed, which changes how their exponent passes are laid out).
+std::shared_ptr<TcSolvePlan> get_tc_solve_plan(const fmmlu_handle* H, SolvePlan& P, int nrhs,
+                                               bool adjoint, cudaStream_t st) {
+  const auto key = std::make_pair(nrhs, adjoint ? 1 : 0);
+  auto it = P.tc.find(key);
+  if (it != P.tc.end()) return it->second;
+  auto tp = std::make_shared<TcSolvePlan>();
+  const size_t nbx = H->sboxes.size();
+  std::vector<TcBoxHost> tbC(std::max<size_t>(1, nbx)), tbT(std::max<size_t>(1, nbx));
+  std::vector<TcUnit> units;
+  for (const SweepSeg& sg : P.segs) {
+    std::vector<TcBoxSize> bs(sg.nb);
+    int64_t so = 0, eo = 0, so2 = 0, eo2 = 0;
+    for (int q = 0; q < sg.nb; ++q) {
+      const SolveBox& sb = H->sboxes[sg.b0 + q];
+      bs[q] = TcBoxSize{0, sb.s, sb.r, sb.n, 0, 0, nrhs};
+      plan_tc_box(sb.s + sb.n, nrhs, sb.r, 7, so, eo, tbC[sg.b0 + q]);
+      plan_tc_box(sb.r, nrhs, sb.s + sb.n, 7, so2, eo2, tbT[sg.b0 + q]);
+    }
+    tp->slice_bytes = std::max(tp->slice_bytes, std::max(so, so2));
+    tp->expo_ints = std::max(tp->expo_ints, std::max(eo, eo2));
+    TcPlan pc{}, pt{};
+    tc_plan(adjoint ? kTcSvCA : kTcSvC, bs, units, pc);
+    tc_plan(adjoint ? kTcSvTA : kTcSvT, bs, units, pt);
+    tp->plC.push_back(pc);
+    tp->plT.push_back(pt);
+  }
+  if (units.empty()) units.push_back(TcUnit{0, 0, 0, 0});
+  tp->d_units = tp->mem.up(units, st);
+  tp->d_tbC = tp->mem.up(tbC, st);
+  tp->d_tbT = tp->mem.up(tbT, st);
+  P.tc[key] = tp;
+  return tp;
 }
 
 // Proxy points per sphere of radius rho (Sec. 5.2: n_gamma from multipole
@@ -818,6 +888,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   H->profile = opt.profile != 0;
   H->chunk0 = opt.solve_chunk > 0 ? opt.solve_chunk : kSweepChunkDefault;
   H->solve_graph = opt.solve_graph;
+  H->solve_tc_nrhs = opt.solve_tc_nrhs;
   H->autotune = opt.solve_chunk == 0 ? opt.autotune : 0;
   H->tune_cache = opt.autotune_cache ? opt.autotune_cache : "";
   ProfScope prof_scope(H->profile ? &H->prof : nullptr);
@@ -831,6 +902,12 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   DevPool work;   // freed at the end of the factorization
   UnitBuf gram_units, elim_units;   // launch lists of the tcgen05 path
   ScratchPool level_scratch;
+  struct Ev {
+    cudaEvent_t e = nullptr;
+    ~Ev() { if (e) cudaEventDestroy(e); }
+  } ev_run_holder;
+  CK(cudaEventCreateWithFlags(&ev_run_holder.e, cudaEventDisableTiming));
+  cudaEvent_t ev_run = ev_run_holder.e;
   H->d_perm = H->mem.get<int>((size_t)n);
   CK(cudaMemcpyAsync(H->d_perm, tree->d_perm, n * sizeof(int), cudaMemcpyDeviceToDevice, st));
   double* soa = work.get<double>((size_t)n * 8);
@@ -858,6 +935,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     }
     stream_wait(st);   // the merge has read the previous level
     const auto setup0 = std::chrono::steady_clock::now();
+    auto sub0 = setup0;
     prev.reset();
     // stop rule: any level box with active far DOFs?
     const int nb = (int)HL.boxes.size();
@@ -927,6 +1005,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (e == 0 || HL.colour[HL.order[e - 1]] != HL.colour[r]) seg_start.push_back(e);
     }
     seg_start.push_back(nb);
+    ht.setup_desc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sub0).count();
+    sub0 = std::chrono::steady_clock::now();
     // pool offsets of the blocks between the boxes of each closed
     // neighbourhood {B} u N(B), and of the blocks (q, B), (B, q) for q in Q(B)
     pairtab.resize((size_t)ptab_size);
@@ -948,6 +1028,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         }
       }
     });
+    ht.setup_pairs += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sub0).count();
+    sub0 = std::chrono::steady_clock::now();
     // per-colour scratch offsets (reset at each colour start)
     int64_t rows_max = 0, M_max = 0, W_max = 0;
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
@@ -1235,6 +1317,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     OzBoxHost* d_ozb = use_mma ? lw.up(ozb, st) : nullptr;
     void* d_oz_slices = use_mma ? (void*)lw.get<uint16_t>((size_t)oz_slices) : nullptr;
     int* d_oz_expo = use_mma ? lw.get<int>((size_t)oz_expo) : nullptr;
+    ht.setup_plans += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - sub0).count();
+    sub0 = std::chrono::steady_clock::now();
     CpqrPart* d_parts = lw.up(parts, st);
     unsigned char* d_cpqr_scratch = lw.get<unsigned char>((size_t)cpqr_scratch);
     unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
@@ -1293,7 +1377,16 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (use_tc) {
         CK(cudaMemcpyAsync(h_run + b0, d_run + b0, cnt * sizeof(BoxRun), cudaMemcpyDeviceToHost,
                            st));
-        stream_wait(st);
+        CK(cudaEventRecord(ev_run, st));
+      }
+      // the elimination blocks need no plan: the GPU assembles them while the
+      // host waits for the ranks and plans the products
+      launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
+      if (use_tc) {
+        {
+          HostTimer wt(&HostTimes::wait);
+          CK(cudaEventSynchronize(ev_run));
+        }
         HostTimer pt(&HostTimes::plan);
         std::vector<TcBoxSize> bs(cnt);
         for (int e = 0; e < cnt; ++e) {
@@ -1316,7 +1409,6 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         }
         elim_units.upload(units, st);
       }
-      launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
       const int kskip = use_tc ? kTcInnerMin : use_oz ? kOzInnerMin : 0;
       // the fp64 FMA products take the boxes whose inner dimension is below
       // kskip; with the tcgen05 path (kskip = 1) only empty products are
@@ -1627,7 +1719,9 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
      << ", \"colour_segments\": " << H->sseg.size() << ", \"host_ms\": {\"alloc\": " << ht.alloc
      << ", \"allocs\": " << ht.allocs << ", \"release\": " << ht.release
      << ", \"wait\": " << ht.wait << ", \"make_level\": " << ht.make_level
-     << ", \"plan\": " << ht.plan << ", \"level_setup\": " << ht.setup << "}}";
+     << ", \"plan\": " << ht.plan << ", \"level_setup\": " << ht.setup
+     << ", \"setup_desc\": " << ht.setup_desc << ", \"setup_pairs\": " << ht.setup_pairs
+     << ", \"setup_plans\": " << ht.setup_plans << "}}";
   H->stats = js.str();
 }
 
@@ -1653,6 +1747,10 @@ size_t counter_bytes(const fmmlu_handle* H, int nrhs) {
 
 void alloc_ctx(const fmmlu_handle* H, SolveCtx& c) {
   const int64_t n = H->n;
+  if (c.tcp) {
+    c.tslices = c.mem.get<unsigned char>((size_t)c.tcp->slice_bytes);
+    c.texpo = c.mem.get<int>((size_t)c.tcp->expo_ints);
+  }
   c.v = c.mem.get<double2>((size_t)n * c.nrhs);
   c.part = c.mem.get<double2>((size_t)c.plan->part_max * c.nrhs);
   c.cnt = c.mem.get<int>(counter_bytes(H, c.nrhs) / sizeof(int));
@@ -1667,18 +1765,46 @@ void alloc_ctx(const fmmlu_handle* H, SolveCtx& c) {
 void run_sweeps(const fmmlu_handle* H, const SolveCtx& c, cudaStream_t st) {
   const SolvePlan& P = *c.plan;
   const int64_t n = H->n, pst = P.part_max;
+  const TcSolvePlan* tp = c.tcp.get();
+  LevelDev Ls;   // context of the tensor-core C products
+  std::memset(&Ls, 0, sizeof(Ls));
+  if (tp) {
+    Ls.desc = P.d_desc;
+    Ls.run = P.d_run;
+    Ls.status = P.d_status;
+    Ls.sbox = P.d_boxes;
+    Ls.sv = c.v;
+    Ls.sn = n;
+    Ls.snrhs = c.nrhs;
+    Ls.spart = c.part;
+    Ls.spst = pst;
+  }
   CK(cudaMemsetAsync(c.cnt, 0, counter_bytes(H, c.nrhs), st));
-  for (const auto& sg : P.segs)
+  for (size_t q = 0; q < P.segs.size(); ++q) {
+    const SweepSeg& sg = P.segs[q];
     launch_sweep(P.d_boxes, P.d_items, sg, c.v, n, c.nrhs, false, c.adjoint, c.part, pst, st,
-                 c.cnt);
+                 c.cnt, tp != nullptr);
+    if (tp) {
+      launch_tc_planned(c.adjoint ? kTcSvCA : kTcSvC, Ls, sg.b0, tp->d_tbC + sg.b0, c.tslices,
+                        c.texpo, nullptr, nullptr, false, tp->d_units, tp->plC[q], st);
+      launch_copy_z(P.d_boxes, sg.b0, sg.nb, sg.rmax, c.v, n, c.nrhs, c.part, pst, st);
+    }
+  }
   if (H->n0 > 0) {
     launch_root_gather(c.v, H->d_root_dofs, H->n0, n, c.nrhs, c.vr, st);
     CK(launch_root_solve(H->d_root, H->n0, H->nb_root, c.vr, c.z, c.rscr, c.nrhs, c.adjoint, st));
     launch_root_scatter(c.vr, H->d_root_dofs, H->n0, n, c.nrhs, c.v, st);
   }
-  for (auto it = P.segs.rbegin(); it != P.segs.rend(); ++it)
-    launch_sweep(P.d_boxes, P.d_items, *it, c.v, n, c.nrhs, true, c.adjoint, c.part, pst, st,
-                 c.cnt);
+  // t slots start at zero (a box with an empty C gets no product)
+  if (tp) CK(cudaMemsetAsync(c.part, 0, sizeof(double2) * (size_t)pst * c.nrhs, st));
+  for (size_t q = P.segs.size(); q-- > 0;) {
+    const SweepSeg& sg = P.segs[q];
+    if (tp)
+      launch_tc_planned(c.adjoint ? kTcSvTA : kTcSvT, Ls, sg.b0, tp->d_tbT + sg.b0, c.tslices,
+                        c.texpo, nullptr, nullptr, false, tp->d_units, tp->plT[q], st);
+    launch_sweep(P.d_boxes, P.d_items, sg, c.v, n, c.nrhs, true, c.adjoint, c.part, pst, st,
+                 c.cnt, tp != nullptr);
+  }
 }
 
 // Record the sweeps of c into a CUDA graph on the handle's own capture stream
@@ -1722,6 +1848,8 @@ SolveCtx* get_ctx(const fmmlu_handle* H, int nrhs, bool adjoint, cudaStream_t st
   c->adjoint = adjoint;
   c->stream = st;
   c->plan = get_plan(H, chunk, st);
+  if (H->solve_tc_nrhs > 0 && nrhs >= H->solve_tc_nrhs)
+    c->tcp = get_tc_solve_plan(H, *c->plan, nrhs, adjoint, st);
   alloc_ctx(H, *c);
   CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
   H->ctxs.push_back(std::move(c));
@@ -1748,6 +1876,8 @@ int tune_solve_chunk(const fmmlu_handle* H, int nrhs, bool adjoint, const double
     t.nrhs = nrhs;
     t.adjoint = adjoint;
     t.plan = get_plan(H, chunk, st);
+    if (H->solve_tc_nrhs > 0 && nrhs >= H->solve_tc_nrhs)
+      t.tcp = get_tc_solve_plan(H, *t.plan, nrhs, adjoint, st);
     alloc_ctx(H, t);
     float tmin = INFINITY;
     for (int rep = 0; rep < 4; ++rep) {
@@ -1787,12 +1917,23 @@ int choose_chunk(const fmmlu_handle* H, int nrhs, bool adjoint, const double* b,
 
 // Algorithmic flops and bytes of one solve (both sweeps and the root) for the
 // per-kernel accounting of a profiled handle.
-void account_solve(const fmmlu_handle* H, const SolvePlan& plan, int nrhs) {
+void account_solve(const fmmlu_handle* H, const SolvePlan& plan, int nrhs, bool tc = false) {
   for (const auto& sg : plan.segs) {
     H->prof.add_work("sweep_fwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
-    H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
     H->prof.add_work("sweep_bwd", sg.flops_b * nrhs, sg.bytes_b + sg.bytes_per_rhs * nrhs / 2);
-    H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+    if (!tc) {
+      H->prof.add_work("sweep_fwd_c", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+      H->prof.add_work("sweep_bwd_t", sg.flops_c * nrhs, sg.bytes_c + sg.bytes_per_rhs * nrhs / 2);
+      continue;
+    }
+    // exact split: 28 digit pairs x 4 real products per complex multiply-add
+    // (8 fp64 flops); the stored block is split on every solve (read twice,
+    // 28 B of digits written and read back per entry)
+    const double entries = sg.bytes_c / 16.0;
+    for (const char* nm : {"sweep_c_tc", "sweep_t_tc"})
+      H->prof.add_work(nm, 28.0 * sg.flops_c * nrhs, 28.0 * entries + sg.bytes_per_rhs * nrhs / 2,
+                       sg.flops_c * nrhs);
+    H->prof.add_work("tc_split", 0, 2.0 * entries * (32.0 + 28.0));
   }
   const int n0 = H->n0;
   for (int i0 = 0; i0 < n0; i0 += H->nb_root) {
@@ -1841,7 +1982,7 @@ void solve_impl(const fmmlu_handle* H, const double* b, double* x, int nrhs, boo
   if (H->profile) {
     CK(cudaStreamSynchronize(st));
     H->prof.resolve();
-    account_solve(H, *c->plan, nrhs);
+    account_solve(H, *c->plan, nrhs, c->tcp != nullptr);
   }
 }
 

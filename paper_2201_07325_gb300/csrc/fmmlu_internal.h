@@ -65,6 +65,8 @@ struct BoxRun {     // device-written results per processed box
   int s, r, n, nq;
 };
 
+struct SolveBox;
+
 struct LevelDev {   // device state of a level
   const BoxDesc* desc;
   BoxRun* run;
@@ -99,6 +101,14 @@ struct LevelDev {   // device state of a level
   double2* root_W;   // later x r, ld later
   int64_t root_n0;
   int root_i0, root_r;
+  // C products of the solve sweeps on the tensor cores: the LevelDev of a
+  // solve plan, whose desc/run are placeholder arrays indexed like sbox
+  const SolveBox* sbox;
+  double2* sv;       // permuted right-hand sides, N x nrhs
+  int64_t sn;
+  int snrhs;
+  double2* spart;    // partial-sum area (z and t slots), stride spst per rhs
+  int64_t spst;
 };
 constexpr int kNsMin = 32;      // smallest r refined on the tensor cores
 
@@ -234,7 +244,11 @@ void plan_tc_box(int mrows, int ncols, int k, int ns, int64_t& slice_off, int64_
 size_t tc_smem_bytes(int ns);
 // problems of the tcgen05 path
 enum { kTcG1 = 0, kTcG3 = 1, kTcW = 2, kTcSchur = 3, kTcXrr = 4, kTcGram = 5, kTcNsY = 6,
-       kTcNsX = 7, kTcRootW = 8, kTcRootS = 9 };
+       kTcNsX = 7, kTcRootW = 8, kTcRootS = 9,
+       // solve sweeps: b_C -= op(X_CR) z (forward) and t = op(X_RC) x_C
+       // (backward), op = identity or, for the adjoint (suffix A), the
+       // conjugate transpose of the other block
+       kTcSvC = 10, kTcSvT = 11, kTcSvCA = 12, kTcSvTA = 13 };
 struct TcUnit {          // one CTA of a tcgen05-path launch
   int box;               // box index relative to the colour's first box
   int side;              // 0 = A operand, 1 = B operand (split launches); product
@@ -244,6 +258,7 @@ struct TcUnit {          // one CTA of a tcgen05-path launch
 struct TcBoxSize {       // exact (or bounding) sizes of one box on the host
   int a, s, r, n, kgram;
   int nsmax;             // largest r refined by Newton-Schulz
+  int nrhs;              // right-hand sides (solve products)
 };
 struct TcPlan {          // the five launches of one problem: offsets into the unit list
   int off[5], cnt[5];    // exponents A, B; digits A, B; product tiles
@@ -303,10 +318,16 @@ void launch_scatter_vec(const double2* v, const int* perm, int64_t n, int nrhs,
                         double2* x, cudaStream_t st);
 // one-time kernel attributes of the sweeps (call before a stream capture)
 void prepare_solve_kernels();
-// cnt: one int per eliminated box and right-hand side, zero between sweeps
+// cnt: one int per eliminated box and right-hand side, zero between sweeps.
+// skip_c: leave out the C product (k_fwd_c / k_bwd_t) because the caller
+// runs it on the tensor cores (forward: then launch_copy_z stores b_R = z)
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
-                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt);
+                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt,
+                  bool skip_c = false);
+// b_R = z for the boxes [b0, b0 + nb) (z in the boxes' z slots)
+void launch_copy_z(const SolveBox* boxes, int b0, int nb, int rmax, double2* v, int64_t n,
+                   int nrhs, const double2* partial, int64_t pstride, cudaStream_t st);
 void launch_root_gather(const double2* v, const int* dofs, int n0, int64_t n,
                         int nrhs, double2* vr, cudaStream_t st);
 void launch_root_scatter(const double2* vr, const int* dofs, int n0, int64_t n,

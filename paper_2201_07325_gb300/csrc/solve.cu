@@ -344,9 +344,27 @@ static void set_smem_attr() {
 
 void prepare_solve_kernels() { set_smem_attr(); }
 
+// b_R = z (forward sweep with the C product on the tensor cores)
+__global__ void k_copy_z(const SolveBox* __restrict__ boxes, int b0, double2* __restrict__ v,
+                         int64_t n, const double2* __restrict__ partial, int64_t pstride) {
+  const SolveBox B = boxes[b0 + blockIdx.x];
+  const int j = blockIdx.y;
+  double2* vc = v + j * n;
+  const double2* z = partial + j * pstride + B.zoff;
+  for (int k = threadIdx.x; k < B.r; k += blockDim.x) vc[B.idx[k]] = z[k];
+}
+
+void launch_copy_z(const SolveBox* boxes, int b0, int nb, int rmax, double2* v, int64_t n,
+                   int nrhs, const double2* partial, int64_t pstride, cudaStream_t st) {
+  if (nb <= 0) return;
+  const int th = rmax >= 256 ? 256 : rmax >= 64 ? 128 : 64;
+  FMMLU_LAUNCH("sweep_fwd", st,
+               k_copy_z<<<dim3(nb, nrhs), th, 0, st>>>(boxes, b0, v, n, partial, pstride));
+}
+
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
-                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt) {
+                  double2* partial, int64_t pstride, cudaStream_t st, int* cnt, bool skip_c) {
   if (sg.nb <= 0) return;
   set_smem_attr();
   const int adj = adjoint ? 1 : 0;
@@ -360,13 +378,16 @@ void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg&
     FMMLU_LAUNCH("sweep_fwd", st,
                  k_sw_z<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
                                                              partial, pstride, adj));
-    FMMLU_LAUNCH("sweep_fwd_c", st,
-                 k_fwd_c<<<dim3(sg.ni, nrhs), 256, smr, st>>>(boxes, items, sg.i0, v, n,
-                                                             partial, pstride, adj));
+    if (!skip_c)
+      FMMLU_LAUNCH("sweep_fwd_c", st,
+                   k_fwd_c<<<dim3(sg.ni, nrhs), 256, smr, st>>>(boxes, items, sg.i0, v, n,
+                                                               partial, pstride, adj));
   } else {
     const size_t sm1 = red + (size_t)sg.chunk * sizeof(double2);
-    FMMLU_LAUNCH("sweep_bwd_t", st, k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
-                                                                               partial, pstride, cnt, adj));
+    if (!skip_c)
+      FMMLU_LAUNCH("sweep_bwd_t", st,
+                   k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
+                                                                 partial, pstride, cnt, adj));
     FMMLU_LAUNCH("sweep_bwd", st,
                  k_sw_xr<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
                                                               partial, pstride, adj));

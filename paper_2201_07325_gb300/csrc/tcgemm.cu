@@ -407,6 +407,65 @@ struct TcRootS {
   }
 };
 
+// The C products of the solve sweeps (Sec. 4.2, factored form of A^{-1}) for
+// one colour of the solve plan, all right-hand sides at once. The box is the
+// index of the placeholder descriptor d in L.desc, which is also its index in
+// L.sbox. Forward: b_C -= op(X_CR) z with z in the box's z slots (op(X_CR) =
+// X_CR, or X_RC^H for the adjoint); backward: t = op(X_RC) x_C into the box's
+// t slots (X_RC, or X_CR^H). Rows of C are DOFs idx[r ..], rows of R idx[0 ..].
+__device__ __forceinline__ const SolveBox& sv_box(const LevelDev& L, const BoxDesc& d) {
+  return L.sbox[&d - L.desc];
+}
+__device__ __forceinline__ double2 sv_conj(double2 v) { return make_double2(v.x, -v.y); }
+
+template <bool Adj>
+struct TcSvC {
+  static constexpr bool kConj = false, kUpper = false, kAk = Adj, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun&, int& m, int& n,
+                              int& k) {
+    const SolveBox& B = sv_box(L, d);
+    m = B.s + B.n; n = L.snrhs; k = B.r;
+    return B.r >= kTcInnerMin && m > 0;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    const SolveBox& B = sv_box(L, d);
+    return Adj ? sv_conj(B.XRC[kk + (int64_t)i * B.ldU]) : B.XCR[i + (int64_t)kk * B.ldL];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    return L.spart[j * L.spst + sv_box(L, d).zoff + kk];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    const SolveBox& B = sv_box(L, d);
+    double2* p = L.sv + j * L.sn + B.idx[B.r + i];
+    const double2 o = *p;
+    *p = make_double2(o.x - vr, o.y - vi);
+  }
+};
+
+template <bool Adj>
+struct TcSvT {
+  static constexpr bool kConj = false, kUpper = false, kAk = Adj, kBk = true;
+  __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun&, int& m, int& n,
+                              int& k) {
+    const SolveBox& B = sv_box(L, d);
+    m = B.r; n = L.snrhs; k = B.s + B.n;
+    return B.r > 0 && k >= kTcInnerMin;
+  }
+  __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
+    const SolveBox& B = sv_box(L, d);
+    return Adj ? sv_conj(B.XCR[kk + (int64_t)i * B.ldL]) : B.XRC[i + (int64_t)kk * B.ldU];
+  }
+  __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
+    const SolveBox& B = sv_box(L, d);
+    return L.sv[j * L.sn + B.idx[B.r + kk]];
+  }
+  __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra&,
+                             int i, int j, double vr, double vi) {
+    L.spart[j * L.spst + sv_box(L, d).toff + i] = make_double2(vr, vi);
+  }
+};
+
 // G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
 template <typename CM>
 struct TcGram {
@@ -941,12 +1000,17 @@ static bool tc_dims_host(int which, const TcBoxSize& z, int& m, int& n, int& k) 
     // root step: a = later DOFs, r = block width
     case kTcRootW: m = z.a; n = z.r; k = z.r; return z.a > 0 && z.r >= kTcInnerMin;
     case kTcRootS: m = z.a; n = z.a; k = z.r; return z.a > 0 && z.r >= kTcInnerMin;
+    // solve sweeps (per colour of the solve plan)
+    case kTcSvC:
+    case kTcSvCA: m = z.s + z.n; n = z.nrhs; k = z.r; return z.r >= kTcInnerMin && m > 0;
+    case kTcSvT:
+    case kTcSvTA: m = z.r; n = z.nrhs; k = z.s + z.n; return z.r > 0 && k >= kTcInnerMin;
   }
   return false;
 }
 
 static bool tc_kcontig(int which, bool side_b) {
-  return side_b || which == kTcG1 || which == kTcGram;
+  return side_b || which == kTcG1 || which == kTcGram || which == kTcSvCA || which == kTcSvTA;
 }
 
 void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>& units,
@@ -1031,6 +1095,10 @@ void launch_tc_planned(int which, const LevelDev& L, int b0, const TcBoxHost* d_
     case kTcNsX: launch_tc<TcNsX, 7, 6>("ns_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcRootW: launch_tc<TcRootW, 7, 6>("root_w_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcRootS: launch_tc<TcRootS, 7, 6>("root_schur_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcSvC: launch_tc<TcSvC<false>, 7, 6>("sweep_c_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcSvCA: launch_tc<TcSvC<true>, 7, 6>("sweep_c_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcSvT: launch_tc<TcSvT<false>, 7, 6>("sweep_t_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
+    case kTcSvTA: launch_tc<TcSvT<true>, 7, 6>("sweep_t_tc", L, b0, d_tb, slices, expo, x, d_units, pl, st); break;
     case kTcGram:
       if (fp32) launch_tc<TcGram<float2>, 4, 4>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);
       else launch_tc<TcGram<double2>, 7, 6>("gram", L, b0, d_tb, slices, expo, x, d_units, pl, st);

@@ -454,3 +454,38 @@ def test_invalid_arguments(pkg):
     with pytest.raises(pkg.FmmluError):
         pkg.Factorization(bad, s.normals, s.weights, 1.0, 1e-6)
     fac.free()
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-14])
+def test_tensor_core_sweeps_equal_fp64_sweeps(pkg, ell, eps):
+    """With 16 right-hand sides the products with the C blocks of the sweeps
+    run on the tensor cores (exact split); they must agree with the fp64
+    sweeps to rounding, solve and adjoint, eager and replayed as a graph,
+    and at eps -> 0 reproduce the dense solve."""
+    s, A, b, xd = ell
+    rng = np.random.default_rng(16)
+    Bm = rng.standard_normal((16, s.n)) + 1j * rng.standard_normal((16, s.n))
+    Bm[0] = b
+    bt = torch.from_numpy(Bm).to("cuda")
+    out = {}
+    for tc in (8, 0):
+        fac = _gpu_factor(pkg, s, K, eps, leaf_size=24, precision=pkg.PRECISION_FP64,
+                          solve_tc_nrhs=tc)
+        xs, ys = [], []
+        for _ in range(3):                      # eager, captured, replayed
+            x = torch.empty_like(bt)
+            y = torch.empty_like(bt)
+            pkg.fmmlu_solve(fac.handle, bt, x, s.n)
+            pkg.fmmlu_solve_adjoint(fac.handle, bt, y, s.n)
+            xs.append(x)
+            ys.append(y)
+        torch.cuda.synchronize()
+        fac.free()
+        assert torch.equal(xs[0], xs[1]) and torch.equal(xs[0], xs[2])
+        assert torch.equal(ys[0], ys[1]) and torch.equal(ys[0], ys[2])
+        out[tc] = (xs[0].cpu().numpy(), ys[0].cpu().numpy())
+    for k in range(2):
+        a, f = out[8][k], out[0][k]
+        assert np.linalg.norm(a - f) <= 1e-12 * np.linalg.norm(f)
+    if eps < 1e-10:
+        assert np.linalg.norm(out[8][0][0] - xd) <= 1e-10 * np.linalg.norm(xd)
