@@ -1105,7 +1105,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     }
     // CPQR plan per colour: boxes share the co-resident CTAs in proportion to
     // their work (rows x a^2); colours with many boxes use one CTA per box.
-    struct ColPlan { int pbeg = 0, np = 0; int64_t scratch = 0; bool dist = false; int cl = 0; };
+    struct ColPlan { int pbeg = 0, np = 0; int64_t scratch = 0; bool dist = false; };
     // colours whose largest box exceeds the pivoted Cholesky's shared memory
     // take the Householder QR
     std::vector<char> gram_col(seg_start.size(), 0);
@@ -1217,8 +1217,12 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         int amax = 1;
         for (int e = b0; e < b0 + cnt; ++e) {
           plan_gram_box(desc[e].a, desc[e].mmax, H->fp32, so, eo, go, gbh[e]);
-          if (gram_tc)
+          if (gram_tc) {
             plan_tc_box(desc[e].a, desc[e].a, desc[e].mmax, H->fp32 ? 4 : 7, tso, teo, gtb[e]);
+            // G = M^H M: the rows of A and the columns of B are both the
+            // columns of M, so one exponent per column serves both sides
+            gtb[e].eb_off = gtb[e].ea_off;
+          }
           amax = std::max(amax, desc[e].a);
         }
         gr_slices = std::max(gr_slices, gram_tc ? tso : 2 * so);   // bytes
@@ -1229,20 +1233,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         int tot = cnt;
         ColPlan& pp = pplan[sgi];
         pp.dist = cnt <= cap;
-        // a colour with few boxes: one thread-block cluster per box (hardware
-        // barriers, candidates in distributed shared memory), as many CTAs
-        // as fill the GPU, at least 8 columns per CTA
-        int pcl = 1;
         if (pp.dist) {
-          const int pmax = std::min(pchol_cluster_max(amax), std::max(1, (amax + 7) / 8));
-          while (2 * pcl <= pmax && (int64_t)cnt * 2 * pcl <= cap) pcl *= 2;
-        }
-        if (pcl >= 2) {
-          pp.dist = false;
-          pp.cl = pcl;
-          std::fill(P.begin(), P.end(), pcl);
-          tot = cnt * pcl;
-        } else if (pp.dist) {
           double wsum = 0;
           for (int e = b0; e < b0 + cnt; ++e) wsum += std::pow((double)desc[e].a, 3.0);
           tot = 0;
@@ -1374,12 +1365,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
           launch_gram(LD, b0, cnt, d_gbh, d_gr_slices, d_gr_expo, d_gr_g, amax, mmax, H->fp32, st);
         CK(cudaGetLastError());
         CK(cudaMemsetAsync(d_pc_scratch, 0, (size_t)pplan[sgi].scratch, st));
-        if (pplan[sgi].cl >= 2)
-          CK(launch_pchol_cluster(LD, d_parts + pplan[sgi].pbeg, pplan[sgi].np, pplan[sgi].cl,
-                                  d_pc_scratch, d_gbh, d_gr_g, amax, st));
-        else
-          CK(launch_pchol(LD, d_parts + pplan[sgi].pbeg, pplan[sgi].np, d_pc_scratch, d_gbh,
-                          d_gr_g, amax, pplan[sgi].dist, st));
+        CK(launch_pchol(LD, d_parts + pplan[sgi].pbeg, pplan[sgi].np, d_pc_scratch, d_gbh,
+                        d_gr_g, amax, pplan[sgi].dist, st));
       } else if (cplan[sgi].dist) {
         CK(cudaMemsetAsync(d_cpqr_scratch, 0, (size_t)cplan[sgi].scratch, st));
         CK(launch_cpqr_dist(LD, d_parts + cplan[sgi].pbeg, cplan[sgi].np, d_cpqr_scratch, amax,

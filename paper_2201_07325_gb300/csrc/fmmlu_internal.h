@@ -233,13 +233,6 @@ int pchol_capacity(int amax);
 cudaError_t launch_pchol(const LevelDev& L, const CpqrPart* d_parts, int nparts,
                          unsigned char* scratch, const GramBoxHost* d_gb, double2* gbuf, int amax,
                          bool cooperative, cudaStream_t st);
-// largest cluster size (16, 8, 4 or 2; 1 = none) that fits with amax
-int pchol_cluster_max(int amax);
-// one thread-block cluster of P (2..16) CTAs per box; parts: P consecutive
-// entries per box. cudaErrorNotSupported when no cluster of that shape fits.
-cudaError_t launch_pchol_cluster(const LevelDev& L, const CpqrPart* d_parts, int nparts, int P,
-                                 unsigned char* scratch, const GramBoxHost* d_gb, double2* gbuf,
-                                 int amax, cudaStream_t st);
 // tcgemm.cu: exact-split complex products on tcgen05 tensor cores (TMEM
 // accumulators, bulk-copy operand pipeline)
 struct TcBoxHost {       // per box of a colour, planned from bounds

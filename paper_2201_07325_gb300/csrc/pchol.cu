@@ -54,42 +54,9 @@ size_t pchol_smem(int amax) {
   return (size_t)amax * (16 + 4 + 4 + 8) + (size_t)kPcWarps * amax * 16;
 }
 
-// thread-block cluster helpers (distributed shared memory, hardware barrier)
-__device__ __forceinline__ uint32_t pc_cl_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t pc_cl_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void pc_cl_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-__device__ __forceinline__ uint32_t pc_cl_map(const void* p, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
-               : "=r"(r)
-               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ PcCand pc_cl_ld(uint32_t addr) {
-  PcCand c;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(c.val) : "r"(addr) : "memory");
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(c.idx) : "r"(addr + 8u) : "memory");
-  return c;
-}
-
-// kCl = false: the CTAs of a box are parts[] entries (P = 1: one CTA per box,
-// candidates and barriers in shared memory; P > 1: a cooperative launch with
-// candidates and bounded barriers in global memory). kCl = true: each box is
-// one thread-block cluster (its rank and size from the cluster registers),
-// candidates in every CTA's shared memory read over distributed shared
-// memory, hardware cluster barriers.
-template <bool kCl>
+// The CTAs of a box are parts[] entries: P = 1, one CTA per box with its
+// candidates and barriers in shared memory; P > 1, a cooperative launch with
+// candidates and bounded barriers in global memory.
 __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart* __restrict__ parts,
                                                       unsigned char* scratch,
                                                       const GramBoxHost* __restrict__ gb,
@@ -97,8 +64,8 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const CpqrPart me = parts[blockIdx.x];
   const int b = me.box;
-  const int rank = kCl ? (int)pc_cl_rank() : me.rank;
-  const int P = kCl ? (int)pc_cl_size() : me.P;
+  const int rank = me.rank;
+  const int P = me.P;
   const BoxDesc d = L.desc[b];
   const int a = d.a;
   const int m = 2 * L.run[b].nq + 2 * L.n_proxy;
@@ -111,7 +78,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
   // candidates [2][P] by step parity: in global memory when several CTAs
   // share the box, in shared memory when the CTA is alone
   __shared__ PcCand s_cand[2];
-  PcCand* cand = (kCl || P == 1) ? s_cand : reinterpret_cast<PcCand*>(sc + 16);
+  PcCand* cand = P == 1 ? s_cand : reinterpret_cast<PcCand*>(sc + 16);
   double2* colp = reinterpret_cast<double2*>(smem_raw);
   int* piv = reinterpret_cast<int*>(colp + a);
   int* pos = piv + a;
@@ -126,10 +93,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
 #define BARRIER()                                                                   \
   do {                                                                              \
     ++nbar;                                                                         \
-    if (kCl) {                                                                      \
-      __syncthreads();                                                              \
-      pc_cl_sync();                                                                 \
-    } else if (P == 1) {                                                            \
+    if (P == 1) {                                                                   \
       __syncthreads();                                                              \
     } else if (!box_barrier(ctr, nbar * (unsigned)P, abort_flag, L.status)) {       \
       return;                                                                       \
@@ -149,7 +113,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
     }
     pc_warp_best(bv, bi);
     if (lane == 0) {
-      if (kCl || P == 1) {
+      if (P == 1) {
         cand[par].val = bv;
         cand[par].idx = bi;
       } else {
@@ -177,11 +141,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
       for (int c = lane; c < P; c += 32) {
         double v;
         int i;
-        if (kCl) {
-          const PcCand q = pc_cl_ld(pc_cl_map(&s_cand[par], (uint32_t)c));
-          v = q.val;
-          i = q.idx;
-        } else if (P == 1) {
+        if (P == 1) {
           v = cand[par].val;
           i = cand[par].idx;
         } else {
@@ -242,11 +202,6 @@ __global__ void __launch_bounds__(kPcThreads) k_pchol(LevelDev L, const CpqrPart
     BARRIER();
   }
 #undef BARRIER
-  // no CTA of a cluster leaves while another may still read its candidates
-  if (kCl) {
-    __syncthreads();
-    pc_cl_sync();
-  }
   // taken columns in pivot order, the others by increasing index
   __syncthreads();
   for (int k = tid; k < a; k += blockDim.x) pos[k] = -1;
@@ -316,8 +271,8 @@ int pchol_capacity(int amax) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t sm = pchol_smem(amax);
-  cudaFuncSetAttribute(k_pchol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pchol<false>, kPcThreads, sm);
+  cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pchol, kPcThreads, sm);
   return occ * sms;
 }
 
@@ -327,11 +282,11 @@ cudaError_t launch_pchol(const LevelDev& L, const CpqrPart* d_parts, int nparts,
   if (nparts <= 0) return cudaSuccess;
   const size_t sm = pchol_smem(amax);
   cudaError_t e =
-      cudaFuncSetAttribute(k_pchol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (!cooperative) {
     FMMLU_LAUNCH("pchol", st,
-                 (k_pchol<false><<<nparts, kPcThreads, sm, st>>>(L, d_parts, scratch, d_gb, gbuf)));
+                 (k_pchol<<<nparts, kPcThreads, sm, st>>>(L, d_parts, scratch, d_gb, gbuf)));
     return cudaGetLastError();
   }
   LevelDev Lc = L;
@@ -341,73 +296,8 @@ cudaError_t launch_pchol(const LevelDev& L, const CpqrPart* d_parts, int nparts,
   double2* gq = gbuf;
   void* args[] = {&Lc, &pp, &sp, &gp, &gq};
   FMMLU_LAUNCH("pchol", st,
-               e = cudaLaunchCooperativeKernel((const void*)k_pchol<false>, dim3(nparts),
+               e = cudaLaunchCooperativeKernel((const void*)k_pchol, dim3(nparts),
                                                dim3(kPcThreads), args, sm, st));
-  return e;
-}
-
-int pchol_cluster_max(int amax) {
-  const size_t sm = pchol_smem(amax);
-  if (cudaFuncSetAttribute(k_pchol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  cudaFuncSetAttribute(k_pchol<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaGetLastError();
-  for (int P : {16, 8, 4, 2}) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)P);
-    cfg.blockDim = dim3(kPcThreads);
-    cfg.dynamicSmemBytes = sm;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)P;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pchol<true>, &cfg) == cudaSuccess &&
-        nclusters >= 1)
-      return P;
-    cudaGetLastError();
-  }
-  return 1;
-}
-
-cudaError_t launch_pchol_cluster(const LevelDev& L, const CpqrPart* d_parts, int nparts, int P,
-                                 unsigned char* scratch, const GramBoxHost* d_gb, double2* gbuf,
-                                 int amax, cudaStream_t st) {
-  if (nparts <= 0) return cudaSuccess;
-  if (P < 2 || P > 16 || nparts % P) return cudaErrorInvalidValue;
-  const size_t sm = pchol_smem(amax);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_pchol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  if (P > 8) {
-    e = cudaFuncSetAttribute(k_pchol<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)nparts);
-  cfg.blockDim = dim3(kPcThreads);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)P;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int nclusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&nclusters, k_pchol<true>, &cfg);
-  if (e != cudaSuccess || nclusters < 1) {
-    cudaGetLastError();
-    return cudaErrorNotSupported;   // the caller takes the other path
-  }
-  FMMLU_LAUNCH("pchol", st, e = cudaLaunchKernelEx(&cfg, k_pchol<true>, L, d_parts, scratch, d_gb, gbuf));
   return e;
 }
 

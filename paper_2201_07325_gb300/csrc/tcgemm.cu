@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "device_common.cuh"
 
@@ -620,6 +621,9 @@ __global__ void __launch_bounds__(256) k_tc_exp(LevelDev L, int b0, const TcBoxH
 
 __device__ __forceinline__ uint32_t pack_bf16x2(int lo, int hi) { return tc::bf16_pair(lo, hi); }
 
+template <class Prob> struct TcGramLike { static constexpr bool value = false; };
+template <typename CM> struct TcGramLike<TcGram<CM>> { static constexpr bool value = true; };
+
 // grid: x = 32-row groups, y = k-octet groups of 8 (one per warp), z = boxes
 template <class Prob, int NS, bool SideB>
 __device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
@@ -669,7 +673,12 @@ __device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
       *reinterpret_cast<uint4*>(step + (2 * p) * tc::kAChunk + off) = vr;
       *reinterpret_cast<uint4*>(step + (2 * p + 1) * tc::kAChunk + off) = vi;
     }
-  } else {
+  }
+  // The Gram product's B operand is M itself: column j of B is row j of A
+  // (the same exponent and digits), so the A-side unit writes both layouts
+  if (SideB || TcGramLike<Prob>::value) {
+    const int lpb = (n + tc::kCols - 1) / tc::kCols * tc::kCols;
+    if (row >= lpb) return;
     const int blk = row / tc::kCols, r = row % tc::kCols;
     unsigned char* step = slices + t.b_off + ((int64_t)blk * KS + ks) * NS * tc::kBChunk;
     constexpr int rg = 3 * tc::kCols / 8;   // row groups of the three-part block
@@ -1025,10 +1034,14 @@ void tc_plan(int which, const std::vector<TcBoxSize>& boxes, std::vector<TcUnit>
       const int lpb = (n + tc::kCols - 1) / tc::kCols * tc::kCols;
       const int kg = (2 * ((k + 15) / 16) + 7) / 8;
       if (l < 2) {                       // exponents of side A / B
+        // (the Gram product's B exponents are its A exponents: not recomputed)
+        if (l == 1 && which == kTcGram) continue;
         const int lp = l == 0 ? lpa : lpb;
         const int per = tc_kcontig(which, l == 1) ? 8 : 32;
         for (int x = 0; x < (lp + per - 1) / per; ++x) units.push_back(TcUnit{e, l, x, 0});
       } else if (l < 4) {                // digits of side A / B
+        // (the Gram product's A-side units write the B digits too)
+        if (l == 3 && which == kTcGram) continue;
         const int lp = l == 2 ? lpa : lpb;
         for (int x = 0; x < lp / 32; ++x)
           for (int y = 0; y < kg; ++y) units.push_back(TcUnit{e, l - 2, x, y});
@@ -1062,18 +1075,17 @@ static void launch_tc(const char* name, const LevelDev& L, int b0, const TcBoxHo
                  (k_tc_digits<Prob, NS><<<nd, 256, 0, st>>>(L, b0, d_tb, sl, expo, d_units + pl.off[2])));
   if (pl.cnt[4] <= 0) return;
   const size_t smem = tc_smem_bytes(NS);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tc_gemm<Prob, NS, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  // the shared-memory limit is a per-device attribute: set it once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::once_flag attr_once[64];
+  if (dev >= 0 && dev < 64)
+    std::call_once(attr_once[dev], [smem] {
+      cudaFuncSetAttribute(k_tc_gemm<Prob, NS, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    });
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::min(pl.cnt[4], std::max(sms, 1));   // one persistent CTA per SM
   FMMLU_LAUNCH(name, st,
                (k_tc_gemm<Prob, NS, DMAX><<<grid, tc::kThreads, smem, st>>>(
