@@ -41,6 +41,27 @@ void launch_permute_geometry(const double* pts, const double* nrm, const double*
                k_permute_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pts, nrm, w, perm, n, soa));
 }
 
+__global__ void k_split_geometry(const double* __restrict__ soa, int64_t n, float* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < 3; ++c) {
+    const double x = soa[c * n + i];
+    const float h = (float)x;
+    f[c * n + i] = h;
+    f[(3 + c) * n + i] = (float)(x - (double)h);
+    f[(6 + c) * n + i] = (float)soa[(3 + c) * n + i];
+  }
+  f[9 * n + i] = (float)soa[7 * n + i];
+}
+
+GeometryF launch_split_geometry(const double* soa, int64_t n, float* f, cudaStream_t st) {
+  if (n > 0)
+    FMMLU_LAUNCH("split_geometry", st,
+                 k_split_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(soa, n, f));
+  return GeometryF{f, f + n, f + 2 * n, f + 3 * n, f + 4 * n, f + 5 * n,
+                   f + 6 * n, f + 7 * n, f + 8 * n, f + 9 * n};
+}
+
 // ---------------------------------------------------------------------------
 
 __global__ void k_gather_rows(LevelDev L, int b0) {
@@ -98,9 +119,16 @@ constexpr int kIdRows = 64;   // most half-rows per block (pairs of rows)
 // The rows come in pairs that share a kernel evaluation: row i < nq (A(q_i, b_j),
 // outgoing ring) and row nq + i (A(b_j, q_i), incoming ring, the transpose
 // block); proxy row 2nq + l (K(y_l, b_j)) and 2nq + np + l (G(b_j, y_l)).
+// A block takes `rpb` row pairs of one box; the proxy points of its rows are
+// computed once, before the entries. In single precision (C = float2) the
+// kernel is evaluated from the split fp32 geometry and the Schur updates are
+// added in fp32; in double precision everything is fp64.
 template <typename C>
 __global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
   using R = decltype(C().x);
+  constexpr bool kF = sizeof(R) == 4;
+  __shared__ double s_yd[kIdRows][3];   // rho u_l of the block's proxy rows
+  __shared__ float s_yf[kIdRows][3];
   int b = b0 + blockIdx.y;
   const BoxDesc d = L.desc[b];
   const int nq = L.run[b].nq;
@@ -117,44 +145,78 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
   const double rho = L.proxy_factor * 0.86602540378443864676 * d.h;
   const double cg = sqrt(4.0 * kPi * rho * rho / np);
   const int rows = min(rpb, half - row0);
+  for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+    const int l = row0 + t - nq;
+    if (l >= 0) {
+      double ux, uy, uz;
+      fib_point(l, np, ux, uy, uz);
+      s_yd[t][0] = rho * ux; s_yd[t][1] = rho * uy; s_yd[t][2] = rho * uz;
+      s_yf[t][0] = (float)s_yd[t][0]; s_yf[t][1] = (float)s_yd[t][1];
+      s_yf[t][2] = (float)s_yd[t][2];
+    }
+  }
+  __syncthreads();
   const R kk = (R)g.k, ee = (R)g.eta;
+  // the box centre split like the points (single precision)
+  const float chx = (float)d.cx, chy = (float)d.cy, chz = (float)d.cz;
+  const float clx = (float)(d.cx - (double)chx), cly = (float)(d.cy - (double)chy),
+              clz = (float)(d.cz - (double)chz);
+  const R cgr = (R)cg;
   for (int e = threadIdx.x; e < rows * a; e += blockDim.x) {
-    const int i = row0 + e % rows;
+    const int t = e % rows;
+    const int i = row0 + t;
     const int j = e / rows;
     const int jd = L.act_dof[bbase + j];
     C v_out, v_in;
     int r_out, r_in;
     if (i < nq) {
       const int q = qdof[i];
-      typename CT<R>::T kqb, kbq, gq;
-      // coordinate differences in fp64 (cancellation), the rest in R
-      comb_kernel_pair<R>((R)(g.px[jd] - g.px[q]), (R)(g.py[jd] - g.py[q]), (R)(g.pz[jd] - g.pz[q]),
-                          (R)g.nx[q], (R)g.ny[q], (R)g.nz[q], (R)g.nx[jd], (R)g.ny[jd],
-                          (R)g.nz[jd], kk, ee, kqb, kbq, gq);
-      const R sc = (R)(g.sw[q] * g.sw[jd]);
-      double2 o = to_d2(cscale(kqb, sc)), t = to_d2(cscale(kbq, sc));
+      C kqb, kbq, gq;
+      R sc;
+      if constexpr (kF) {
+        const GeometryF& f = g.f;
+        comb_kernel_pair<float>(fdiff(f.xh, f.xl, jd, q), fdiff(f.yh, f.yl, jd, q),
+                                fdiff(f.zh, f.zl, jd, q), f.nx[q], f.ny[q], f.nz[q], f.nx[jd],
+                                f.ny[jd], f.nz[jd], kk, ee, kqb, kbq, gq);
+        sc = f.sw[q] * f.sw[jd];
+      } else {
+        comb_kernel_pair<double>(g.px[jd] - g.px[q], g.py[jd] - g.py[q], g.pz[jd] - g.pz[q],
+                                 g.nx[q], g.ny[q], g.nz[q], g.nx[jd], g.ny[jd], g.nz[jd], kk, ee,
+                                 kqb, kbq, gq);
+        sc = g.sw[q] * g.sw[jd];
+      }
+      C o = cscale(kqb, sc), tr = cscale(kbq, sc);
       const int64_t off_o = L.qpair[d.qpair + 2 * qloc[i]];
       if (off_o >= 0) {
         const int ldc = L.cur_a0[L.qlist[d.qbeg + qloc[i]]];
-        o = cadd(o, L.delta[off_o + qpos[i] + (int64_t)j * ldc]);
+        o = cadd(o, from_d2<C>(L.delta[off_o + qpos[i] + (int64_t)j * ldc]));
       }
       const int64_t off_i = L.qpair[d.qpair + 2 * qloc[i] + 1];
-      if (off_i >= 0) t = cadd(t, L.delta[off_i + j + (int64_t)qpos[i] * a]);
-      v_out = from_d2<C>(o);
-      v_in = from_d2<C>(t);
+      if (off_i >= 0) tr = cadd(tr, from_d2<C>(L.delta[off_i + j + (int64_t)qpos[i] * a]));
+      v_out = o;
+      v_in = tr;
       r_out = i;
       r_in = nq + i;
     } else {
       const int l = i - nq;
-      double ux, uy, uz;
-      fib_point(l, np, ux, uy, uz);
-      const double yx = d.cx + rho * ux, yy = d.cy + rho * uy, yz = d.cz + rho * uz;
-      typename CT<R>::T kyb, kby, gy;
-      comb_kernel_pair<R>((R)(g.px[jd] - yx), (R)(g.py[jd] - yy), (R)(g.pz[jd] - yz), R(0), R(0),
-                          R(0), (R)g.nx[jd], (R)g.ny[jd], (R)g.nz[jd], kk, ee, kyb, kby, gy);
-      const R sc = (R)(cg * g.sw[jd]);
-      v_out = from_d2<C>(to_d2(cscale(kyb, sc)));   // K(y_l, b_j): outgoing proxy row
-      v_in = from_d2<C>(to_d2(cscale(gy, sc)));     // G(b_j, y_l): incoming proxy row
+      C kyb, kby, gy;
+      R sc;
+      if constexpr (kF) {
+        const GeometryF& f = g.f;
+        const float rx = (f.xh[jd] - chx) + (f.xl[jd] - clx);   // b_j - centre
+        const float ry = (f.yh[jd] - chy) + (f.yl[jd] - cly);
+        const float rz = (f.zh[jd] - chz) + (f.zl[jd] - clz);
+        comb_kernel_pair<float>(rx - s_yf[t][0], ry - s_yf[t][1], rz - s_yf[t][2], 0.f, 0.f, 0.f,
+                                f.nx[jd], f.ny[jd], f.nz[jd], kk, ee, kyb, kby, gy);
+        sc = cgr * f.sw[jd];
+      } else {
+        const double yx = d.cx + s_yd[t][0], yy = d.cy + s_yd[t][1], yz = d.cz + s_yd[t][2];
+        comb_kernel_pair<double>(g.px[jd] - yx, g.py[jd] - yy, g.pz[jd] - yz, 0.0, 0.0, 0.0,
+                                 g.nx[jd], g.ny[jd], g.nz[jd], kk, ee, kyb, kby, gy);
+        sc = cg * g.sw[jd];
+      }
+      v_out = cscale(kyb, sc);   // K(y_l, b_j): outgoing proxy row
+      v_in = cscale(gy, sc);     // G(b_j, y_l): incoming proxy row
       r_out = 2 * nq + l;
       r_in = 2 * nq + np + l;
     }
@@ -163,9 +225,10 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
   }
 }
 
-void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, int mmax_max,
-                        bool fp32, cudaStream_t st) {
-  if (nb <= 0) return;
+cudaError_t launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, int mmax_max,
+                               bool fp32, cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  if (fp32 && !g.f.xh) return cudaErrorInvalidValue;   // single-precision copies not made
   // m = 2 (nq + np) rows, in pairs. Every entry is computed the same way for
   // any blocking, so colours with few boxes get shorter row blocks: the
   // kernel is fp64-bound per SM and needs every SM busy.
@@ -184,6 +247,7 @@ void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb, in
     FMMLU_LAUNCH("assemble_id", st, k_assemble_id<float2><<<grid, 256, 0, st>>>(L, g, b0, rpb));
   else
     FMMLU_LAUNCH("assemble_id", st, k_assemble_id<double2><<<grid, 256, 0, st>>>(L, g, b0, rpb));
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -222,6 +286,10 @@ __device__ __forceinline__ double2 add_delta(const LevelDev& L, const BoxDesc& d
   return v;
 }
 
+// kF: off-diagonal kernel values in fp32 from the split geometry (the mixed
+// path), converted to fp64 before the Schur updates are added; the diagonal
+// (self) entries are always fp64.
+template <bool kF>
 __global__ void __launch_bounds__(256) k_assemble_elim(LevelDev L, Geometry g, int b0) {
   __shared__ double2 t3[kElimT][kElimT + 1];
   const int b = b0 + blockIdx.y;
@@ -240,13 +308,21 @@ __global__ void __launch_bounds__(256) k_assemble_elim(LevelDev L, Geometry g, i
   double2* G3 = L.arena + d.G3_off;
   const int ld3 = a + d.nmax;
   const int li = threadIdx.x & 31;
+  const float kf = (float)g.k, ef = (float)g.eta;
   for (int lj = threadIdx.x >> 5; lj < kElimT; lj += blockDim.x >> 5) {
     const int i = i0 + li, j = j0 + lj;
     if (i < a && j < a + n) {
       const Idx r = bpiv(L, d, perm, i);
       const Idx c = col_idx(L, d, perm, ndof, npos, nloc, s, n, j);
       double2 arc, acr;
-      entry_pair(g, r.dof, c.dof, arc, acr);
+      if (kF && r.dof != c.dof) {
+        float2 fa, fb;
+        entry_pair_f(g.f, kf, ef, r.dof, c.dof, fa, fb);
+        arc = to_d2(fa);
+        acr = to_d2(fb);
+      } else {
+        entry_pair(g, r.dof, c.dof, arc, acr);
+      }
       G1[i + (int64_t)j * a] = add_delta(L, d, arc, r, c);
       t3[lj][li] = add_delta(L, d, acr, c, r);
     }
@@ -259,12 +335,17 @@ __global__ void __launch_bounds__(256) k_assemble_elim(LevelDev L, Geometry g, i
   }
 }
 
-void launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb, int amax,
-                          int nmax_max, cudaStream_t st) {
-  if (nb <= 0) return;
+cudaError_t launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb, int amax,
+                                 int nmax_max, bool fp32, cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  if (fp32 && !g.f.xh) return cudaErrorInvalidValue;   // single-precision copies not made
   const int ti = (amax + kElimT - 1) / kElimT, tj = (amax + nmax_max + kElimT - 1) / kElimT;
   dim3 grid((unsigned)(ti * tj), nb);
-  FMMLU_LAUNCH("assemble_elim", st, k_assemble_elim<<<grid, 256, 0, st>>>(L, g, b0));
+  if (fp32)
+    FMMLU_LAUNCH("assemble_elim", st, k_assemble_elim<true><<<grid, 256, 0, st>>>(L, g, b0));
+  else
+    FMMLU_LAUNCH("assemble_elim", st, k_assemble_elim<false><<<grid, 256, 0, st>>>(L, g, b0));
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

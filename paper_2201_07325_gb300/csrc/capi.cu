@@ -915,6 +915,8 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   CK(cudaGetLastError());
   Geometry g{soa, soa + n, soa + 2 * n, soa + 3 * n, soa + 4 * n, soa + 5 * n, soa + 6 * n,
              soa + 7 * n, k, H->eta};
+  // mixed path: near-field and proxy kernel values in fp32 from split copies
+  if (H->fp32) g.f = launch_split_geometry(soa, n, work.get<float>((size_t)n * 10), st);
   int* d_status = work.get<int>(1);
   CK(cudaMemsetAsync(d_status, 0, sizeof(int), st));
 
@@ -1337,7 +1339,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         nmaxm = std::max(nmaxm, desc[e].nmax);
       }
       launch_gather_rows(LD, b0, cnt, st);
-      launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st);
+      CK(launch_assemble_id(LD, g, b0, cnt, mmax, H->fp32, st));
       if (gram_col[sgi]) {
         if (gram_tc) {
           // Gram tiles from a (exact); the k range (split into chunks whose
@@ -1385,7 +1387,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       }
       // the elimination blocks need no plan: the GPU assembles them while the
       // host waits for the ranks and plans the products
-      launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, st);
+      CK(launch_assemble_elim(LD, g, b0, cnt, amax, nmaxm, H->fp32, st));
       if (use_tc) {
         {
           HostTimer wt(&HostTimes::wait);

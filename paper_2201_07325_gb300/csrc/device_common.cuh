@@ -197,6 +197,26 @@ __device__ __forceinline__ void entry_pair(const Geometry& g, int i, int j, doub
   aji = cscale(kji, sc);
 }
 
+// one coordinate of s - t from the split fp32 copies: the high parts'
+// difference is rounded once, the low parts restore what rounding each
+// coordinate to fp32 dropped
+__device__ __forceinline__ float fdiff(const float* h, const float* l, int s, int t) {
+  return (h[s] - h[t]) + (l[s] - l[t]);
+}
+
+// A(i, j) and A(j, i) of the scaled system (i != j), one kernel evaluation in
+// fp32 (CUDA's fp32 sincos and square root) from the split copies
+__device__ __forceinline__ void entry_pair_f(const GeometryF& f, float k, float eta, int i, int j,
+                                             float2& aij, float2& aji) {
+  float2 kij, kji, gg;
+  comb_kernel_pair<float>(fdiff(f.xh, f.xl, j, i), fdiff(f.yh, f.yl, j, i),
+                          fdiff(f.zh, f.zl, j, i), f.nx[i], f.ny[i], f.nz[i], f.nx[j], f.ny[j],
+                          f.nz[j], k, eta, kij, kji, gg);
+  const float sc = f.sw[i] * f.sw[j];
+  aij = cscale(kij, sc);
+  aji = cscale(kji, sc);
+}
+
 // l-th of n Fibonacci points on the unit sphere
 __device__ __forceinline__ void fib_point(int l, int n, double& ux, double& uy,
                                           double& uz) {

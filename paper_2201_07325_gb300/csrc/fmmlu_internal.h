@@ -30,11 +30,23 @@ enum StatusBits : int {
   kStatusTimeout = 8,    // a bounded inter-CTA wait gave up
 };
 
+// fp32 copies for kernel entries evaluated in single precision (mixed path):
+// each coordinate as a high part (its fp32 rounding) and a low part (the
+// rest, rounded), so that the difference of two points is accurate to fp32
+// relative to the difference itself, however close the points are
+struct GeometryF {
+  const float* xh; const float* yh; const float* zh;
+  const float* xl; const float* yl; const float* zl;
+  const float* nx; const float* ny; const float* nz;
+  const float* sw;
+};
+
 struct Geometry {        // sorted SoA copies of the inputs
   const double* px; const double* py; const double* pz;
   const double* nx; const double* ny; const double* nz;
   const double* w;  const double* sw;
   double k, eta;
+  GeometryF f{};         // null unless the single-precision copies were made
 };
 
 // one per box processed at a level (host-built)
@@ -166,11 +178,15 @@ void launch_end(const char* name, cudaStream_t st);
 // assembly.cu
 void launch_permute_geometry(const double* pts, const double* nrm, const double* w,
                              const int* perm, int64_t n, double* soa, cudaStream_t st);
+// fills the 10 n floats of `fsoa` from the sorted SoA and returns the views
+GeometryF launch_split_geometry(const double* soa, int64_t n, float* fsoa, cudaStream_t st);
 void launch_gather_rows(const LevelDev& L, int b0, int nb, cudaStream_t st);
-void launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb,
-                        int mmax_max, bool fp32, cudaStream_t st);
-void launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb,
-                          int amax, int nmax_max, cudaStream_t st);
+// fp32: kernel values in single precision from g.f (cudaErrorInvalidValue
+// when those copies were not made)
+cudaError_t launch_assemble_id(const LevelDev& L, const Geometry& g, int b0, int nb,
+                               int mmax_max, bool fp32, cudaStream_t st);
+cudaError_t launch_assemble_elim(const LevelDev& L, const Geometry& g, int b0, int nb,
+                                 int amax, int nmax_max, bool fp32, cudaStream_t st);
 struct MergeItem {
   const double2* src; double2* dst;
   int ld_src, ld_dst, off_i, off_j, ni, nj;
