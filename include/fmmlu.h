@@ -156,7 +156,10 @@ typedef struct fmmlu_opts {
                                  arithmetic) on the tcgen05 tensor cores by
                                  the exact split of schur_emulation 1 (the
                                  operands split on every solve); fewer run
-                                 in fp64 FMA. Default 8; 0 = never.        */
+                                 on the CUDA cores in double-float
+                                 arithmetic (every block entry read once per
+                                 group of up to 8 right-hand sides).
+                                 Default 32; 0 = never.                    */
   int proxy_rule;             /* number of proxy points per sphere (Sec. 5.2,
                                  proxy surface discretization):
                                  FMMLU_PROXY_FIXED (default): n_proxy on

@@ -245,7 +245,7 @@ void default_opts(fmmlu_opts* o) {
   o->xrr_refine_tol = 1e-9;
   o->solve_chunk = 0;
   o->solve_graph = 1;
-  o->solve_tc_nrhs = 8;
+  o->solve_tc_nrhs = 32;
   o->autotune = 1;
   o->autotune_cache = nullptr;
 }
@@ -359,7 +359,7 @@ struct fmmlu_handle {
   std::vector<SweepSeg> sseg;     // their colour segments (items not yet built)
   int chunk0 = kSweepChunkDefault;
   int solve_graph = 1, autotune = 0;
-  int solve_tc_nrhs = 8;          // tensor-core C products from this many rhs (0: never)
+  int solve_tc_nrhs = 32;         // tensor-core C products from this many rhs (0: never)
   std::string tune_cache;
   uint64_t shape_key = 0;         // hash of the solve structure (tuning cache key)
   int n0 = 0, nb_root = 64;

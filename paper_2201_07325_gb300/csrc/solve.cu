@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "device_common.cuh"
+#include "dfloat.cuh"
 
 namespace fmmlu {
 
@@ -147,144 +148,285 @@ __device__ __forceinline__ void mv_dots(const double2* __restrict__ M, int64_t l
   }
 }
 
-// forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
-__global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes,
-                                              const SweepItem* __restrict__ items, int i0,
-                                              double2* __restrict__ v, int64_t n, int adjoint) {
-  extern __shared__ double2 sh[];
-  const SweepItem it = items[i0 + blockIdx.x];
-  const SolveBox B = boxes[it.box];
-  double2* vc = v + blockIdx.y * n;
-  double2* bS = sh;
-  const int* Ridx = B.idx + it.c0;
-  const int* Sidx = B.idx + B.r;
-  for (int i = threadIdx.x; i < B.s; i += blockDim.x) bS[i] = vc[Sidx[i]];
-  __syncthreads();
-  const int kc = it.c1 - it.c0;
-  auto st = [=](int o, double2 y) { const int dof = Ridx[o]; vc[dof] = csub(vc[dof], y); };
-  const double2* M = B.T + (int64_t)it.c0 * B.ldT;
-  if (adjoint) mv_dots<true>(M, B.ldT, bS, kc, B.s, st);
-  else mv_dots<false>(M, B.ldT, bS, kc, B.s, st);
+// ---------------------------------------------------------------------------
+// Box sweeps in double-float arithmetic (dfloat.cuh), a group of NR
+// right-hand sides per CTA (blockIdx.y = group): every block entry is read
+// from HBM once per group and split into two fp32 numbers by integer
+// operations, then applied to the NR right-hand sides staged in shared
+// memory (complex double-float, X[cc * xs + q]). The vectors stay fp64; each
+// result is rounded to fp64 once, where it is subtracted or stored.
+
+// y[o][cc] = sum_{q < nq} op(M[o + q ld]) X[cc][q], o < no: the output index
+// is the contiguous one. 256 threads: consecutive threads take consecutive
+// outputs (16 or 32 per tile); when fewer than 256 outputs are left, the
+// remaining threads split q into interleaved groups whose sums meet in red
+// (256 entries, one right-hand side at a time, in a fixed group order).
+template <int NR, bool kCj, class Store>
+__device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t ld,
+                                         const float4* X, int xs, int no, int nq, float4* red,
+                                         Store store) {
+  const int t = threadIdx.x;
+  const int ot = no <= 16 ? 16 : 32;
+  int span = ot;
+  while (span < no && span < 256) span <<= 1;
+  const int qg = 256 / span;
+  const int oi = t % span, g = t / span;
+  for (int ob = 0; ob < no; ob += span) {
+    const int o = ob + oi;
+    DF ar[NR], ai[NR];
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc) ar[cc] = ai[cc] = DF{0.f, 0.f};
+    auto apply = [&](double2 m, int q) {
+      const DF mr = df_split_bits(m.x), mi = df_split_bits(m.y);
+#pragma unroll
+      for (int cc = 0; cc < NR; ++cc) cdf_mac<kCj>(ar[cc], ai[cc], mr, mi, X[cc * xs + q]);
+    };
+    if (o < no) {
+      const double2* Mo = M + o;
+      int q = g;
+      for (; q + qg < nq; q += 2 * qg) {
+        const double2 m0 = Mo[(int64_t)q * ld];
+        const double2 m1 = Mo[(int64_t)(q + qg) * ld];
+        apply(m0, q);
+        apply(m1, q + qg);
+      }
+      if (q < nq) apply(Mo[(int64_t)q * ld], q);
+    }
+    if (qg == 1) {
+      if (o < no)
+#pragma unroll
+        for (int cc = 0; cc < NR; ++cc) store(o, cc, make_double2(df_value(ar[cc]), df_value(ai[cc])));
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < NR; ++cc) {
+        red[t] = make_float4(ar[cc].h, ar[cc].l, ai[cc].h, ai[cc].l);
+        __syncthreads();
+        if (g == 0 && o < no) {
+          DF sr = ar[cc], si = ai[cc];
+          for (int gg = 1; gg < qg; ++gg) {
+            const float4 w = red[gg * span + oi];
+            sr = df_add(sr, DF{w.x, w.y});
+            si = df_add(si, DF{w.z, w.w});
+          }
+          store(o, cc, make_double2(df_value(sr), df_value(si)));
+        }
+        __syncthreads();
+      }
+    }
+  }
 }
 
-// z_k = op(X_RR^{-1})(k, :) y for the chunk's rows k; store(k - c0, z_k)
-template <class Store>
-__device__ __forceinline__ void xinv_rows(const SolveBox& B, int c0, int kc, const double2* y,
-                                          double2* red, bool adjoint, Store store) {
-  if (!adjoint) mv_cols<false>(B.Xinv + c0, B.ldX, y, kc, B.r, red, store);
-  else mv_dots<true>(B.Xinv + (int64_t)c0 * B.ldX, B.ldX, y, kc, B.r, store);
+// y[o][cc] = sum_{q < nq} op(M[q + o ld]) X[cc][q], o < no: every output is a
+// dot product along a contiguous column, taken by a group of 4 to 32 lanes
+// (sized so that every lane takes at least four terms) and summed across
+// the group with shuffles.
+template <int NR, bool kCj, class Store>
+__device__ __forceinline__ void mvr_dots(const double2* __restrict__ M, int64_t ld,
+                                         const float4* X, int xs, int no, int nq, Store store) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int sw = nq >= 128 ? 32 : (nq >= 64 ? 16 : (nq >= 32 ? 8 : 4));
+  const int per = 32 / sw;
+  const int sl = lane % sw, sub = lane / sw;
+  for (int ob = w * per; ob < no; ob += nw * per) {
+    const int o = ob + sub;
+    DF ar[NR], ai[NR];
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc) ar[cc] = ai[cc] = DF{0.f, 0.f};
+    auto apply = [&](double2 m, int q) {
+      const DF mr = df_split_bits(m.x), mi = df_split_bits(m.y);
+#pragma unroll
+      for (int cc = 0; cc < NR; ++cc) cdf_mac<kCj>(ar[cc], ai[cc], mr, mi, X[cc * xs + q]);
+    };
+    if (o < no) {
+      const double2* Mo = M + (int64_t)o * ld;
+      int q = sl;
+      for (; q + sw < nq; q += 2 * sw) {
+        const double2 m0 = Mo[q], m1 = Mo[q + sw];
+        apply(m0, q);
+        apply(m1, q + sw);
+      }
+      if (q < nq) apply(Mo[q], q);
+    }
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc) {
+      const DF sr = df_group_sum(ar[cc], sw), si = df_group_sum(ai[cc], sw);
+      if (sl == 0 && o < no) store(o, cc, make_double2(df_value(sr), df_value(si)));
+    }
+  }
+}
+
+// X[cc][k] = split(value(cc, k)) for k < cnt and the group's right-hand
+// sides (zeros past nrhs)
+template <int NR, class Load>
+__device__ __forceinline__ void stage_rhs(float4* X, int cnt, int cb, int nrhs, Load load) {
+  for (int e = threadIdx.x; e < NR * cnt; e += blockDim.x) {
+    const int cc = e / cnt, k = e - cc * cnt;
+    X[e] = cb + cc < nrhs ? cdf_split_bits(load(cb + cc, k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
+template <int NR>
+__global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes,
+                                              const SweepItem* __restrict__ items, int i0,
+                                              double2* __restrict__ v, int64_t n, int nrhs,
+                                              int adjoint) {
+  extern __shared__ float4 shf[];
+  const SweepItem it = items[i0 + blockIdx.x];
+  const SolveBox B = boxes[it.box];
+  const int cb = blockIdx.y * NR;
+  float4* X = shf;   // NR x s
+  const int* Sidx = B.idx + B.r;
+  stage_rhs<NR>(X, B.s, cb, nrhs, [&](int c, int i) { return v[(int64_t)c * n + Sidx[i]]; });
+  __syncthreads();
+  const int kc = it.c1 - it.c0;
+  const int* Ridx = B.idx + it.c0;
+  auto st = [=](int o, int cc, double2 y) {
+    if (cb + cc >= nrhs) return;
+    double2* p = v + (int64_t)(cb + cc) * n + Ridx[o];
+    *p = csub(*p, y);
+  };
+  const double2* M = B.T + (int64_t)it.c0 * B.ldT;
+  if (adjoint) mvr_dots<NR, true>(M, B.ldT, X, B.s, kc, B.s, st);
+  else mvr_dots<NR, false>(M, B.ldT, X, B.s, kc, B.s, st);
+}
+
+// z_k = op(X_RR^{-1})(k, :) y for the chunk's rows k; store(k - c0, cc, z_k)
+template <int NR, class Store>
+__device__ __forceinline__ void xinv_rows(const SolveBox& B, int c0, int kc, const float4* Y,
+                                          float4* red, bool adjoint, Store store) {
+  if (!adjoint) mvr_cols<NR, false>(B.Xinv + c0, B.ldX, Y, B.r, kc, B.r, red, store);
+  else mvr_dots<NR, true>(B.Xinv + (int64_t)c0 * B.ldX, B.ldX, Y, B.r, kc, B.r, store);
 }
 
 // forward: z = op(X_RR^{-1}) b_R for the chunk's rows, into the box's scratch
+template <int NR>
 __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes,
                                               const SweepItem* __restrict__ items, int i0,
                                               const double2* __restrict__ v, int64_t n,
                                               double2* __restrict__ zbuf, int64_t zstride,
-                                              int adjoint) {
-  extern __shared__ double2 sh[];
+                                              int nrhs, int adjoint) {
+  extern __shared__ float4 shf[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
-  const double2* vc = v + blockIdx.y * n;
-  double2* red = sh;
-  double2* y = sh + 256;        // r
-  for (int k = threadIdx.x; k < B.r; k += blockDim.x) y[k] = vc[B.idx[k]];
+  const int cb = blockIdx.y * NR;
+  float4* red = shf;
+  float4* Y = shf + 256;        // NR x r
+  stage_rhs<NR>(Y, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
-  double2* zo = zbuf + blockIdx.y * zstride + B.zoff + it.c0;
-  xinv_rows(B, it.c0, it.c1 - it.c0, y, red, adjoint != 0,
-            [=](int o, double2 z) { zo[o] = z; });
+  double2* zo = zbuf + B.zoff + it.c0;
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Y, red, adjoint != 0, [=](int o, int cc, double2 z) {
+    if (cb + cc < nrhs) zo[(int64_t)(cb + cc) * zstride + o] = z;
+  });
 }
 
 // backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = the summed partials
+template <int NR>
 __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
                                                const double2* __restrict__ partial,
-                                               int64_t pstride, int adjoint) {
-  extern __shared__ double2 sh[];
+                                               int64_t pstride, int nrhs, int adjoint) {
+  extern __shared__ float4 shf[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
-  double2* vc = v + blockIdx.y * n;
-  const double2* pc = partial + blockIdx.y * pstride;
-  double2* red = sh;
-  double2* tt = sh + 256;       // r
-  for (int k = threadIdx.x; k < B.r; k += blockDim.x) tt[k] = pc[B.toff + k];
+  const int cb = blockIdx.y * NR;
+  float4* red = shf;
+  float4* Tt = shf + 256;       // NR x r
+  stage_rhs<NR>(Tt, B.r, cb, nrhs,
+                [&](int c, int k) { return partial[(int64_t)c * pstride + B.toff + k]; });
   __syncthreads();
   const int* Ridx = B.idx + it.c0;
-  xinv_rows(B, it.c0, it.c1 - it.c0, tt, red, adjoint != 0, [=](int o, double2 y) {
-    const int dof = Ridx[o];
-    vc[dof] = csub(vc[dof], y);
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Tt, red, adjoint != 0, [=](int o, int cc, double2 y) {
+    if (cb + cc >= nrhs) return;
+    double2* p = v + (int64_t)(cb + cc) * n + Ridx[o];
+    *p = csub(*p, y);
   });
 }
 
 // backward: x_S[i] -= sum_k op(T)(i, k) x_R[k] for the chunk's rows i
+template <int NR>
 __global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
-                                               double2* __restrict__ v, int64_t n, int adjoint) {
-  extern __shared__ double2 sh[];
+                                               double2* __restrict__ v, int64_t n, int nrhs,
+                                               int adjoint) {
+  extern __shared__ float4 shf[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
-  double2* vc = v + blockIdx.y * n;
-  double2* red = sh;
-  double2* xr = sh + 256;       // r
-  for (int k = threadIdx.x; k < B.r; k += blockDim.x) xr[k] = vc[B.idx[k]];
+  const int cb = blockIdx.y * NR;
+  float4* red = shf;
+  float4* Xr = shf + 256;       // NR x r
+  stage_rhs<NR>(Xr, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
   const int* Sidx = B.idx + B.r + it.c0;
-  auto st = [=](int o, double2 y) { const int dof = Sidx[o]; vc[dof] = csub(vc[dof], y); };
-  if (adjoint) mv_cols<true>(B.T + it.c0, B.ldT, xr, it.c1 - it.c0, B.r, red, st);
-  else mv_cols<false>(B.T + it.c0, B.ldT, xr, it.c1 - it.c0, B.r, red, st);
+  auto st = [=](int o, int cc, double2 y) {
+    if (cb + cc >= nrhs) return;
+    double2* p = v + (int64_t)(cb + cc) * n + Sidx[o];
+    *p = csub(*p, y);
+  };
+  if (adjoint) mvr_cols<NR, true>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
+  else mvr_cols<NR, false>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
 }
 
 // forward: b_C -= op(X_CR) z on the chunk's rows of C
+template <int NR>
 __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
                                                const double2* __restrict__ zbuf, int64_t zstride,
-                                               int adjoint) {
-  extern __shared__ double2 sh[];
+                                               int nrhs, int adjoint) {
+  extern __shared__ float4 shf[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int r = B.r;
-  double2* vc = v + blockIdx.y * n;
-  const double2* zc = zbuf + blockIdx.y * zstride + B.zoff;
-  double2* red = sh;
-  double2* z = sh + 256;        // r
-  for (int k = threadIdx.x; k < r; k += blockDim.x) {
-    z[k] = zc[k];
-    if (it.c0 == 0) vc[B.idx[k]] = z[k];   // b_R = z, once per box
-  }
+  const int cb = blockIdx.y * NR;
+  float4* red = shf;
+  float4* Z = shf + 256;        // NR x r
+  stage_rhs<NR>(Z, r, cb, nrhs, [&](int c, int k) {
+    const double2 zv = zbuf[(int64_t)c * zstride + B.zoff + k];
+    if (it.c0 == 0) v[(int64_t)c * n + B.idx[k]] = zv;   // b_R = z, once per box
+    return zv;
+  });
   __syncthreads();
   const int* Cidx = B.idx + r + it.c0;
-  auto st = [=](int o, double2 y) { const int dof = Cidx[o]; vc[dof] = csub(vc[dof], y); };
+  auto st = [=](int o, int cc, double2 y) {
+    if (cb + cc >= nrhs) return;
+    double2* p = v + (int64_t)(cb + cc) * n + Cidx[o];
+    *p = csub(*p, y);
+  };
   const int w = it.c1 - it.c0;
-  if (!adjoint) mv_cols<false>(B.XCR + it.c0, B.ldL, z, w, r, red, st);
-  else mv_dots<true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, z, w, r, st);
+  if (!adjoint) mvr_cols<NR, false>(B.XCR + it.c0, B.ldL, Z, r, w, r, red, st);
+  else mvr_dots<NR, true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, Z, r, w, r, st);
 }
 
-// backward: partial = op(X_RC)[:, chunk] x_C[chunk] (r values per chunk);
-// the last chunk of a box to finish (one counter per box and right-hand
-// side, reset by that CTA; no CTA waits) sums the box's partials in chunk
-// order into its t slots
+// backward: partial = op(X_RC)[:, chunk] x_C[chunk] (r values per chunk and
+// right-hand side); the last chunk of a box to finish (one counter per box
+// and right-hand-side group, reset by that CTA; no CTA waits) sums the box's
+// partials in chunk order into its t slots
+template <int NR>
 __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                const double2* __restrict__ v, int64_t n,
                                                double2* __restrict__ partial, int64_t pstride,
-                                               int* __restrict__ cnt, int adjoint) {
+                                               int* __restrict__ cnt, int nrhs, int adjoint) {
   __shared__ int last;
-  extern __shared__ double2 sh[];
+  extern __shared__ float4 shf[];
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int r = B.r;
-  const double2* vc = v + blockIdx.y * n;
+  const int cb = blockIdx.y * NR;
   const int w = it.c1 - it.c0;
-  double2* red = sh;            // 256
-  double2* u = sh + 256;        // chunk values of x_C
+  float4* red = shf;            // 256
+  float4* U = shf + 256;        // NR x w: the chunk's values of x_C
   const int* Cidx = B.idx + r;
-  for (int j = threadIdx.x; j < w; j += blockDim.x) u[j] = vc[Cidx[it.c0 + j]];
+  stage_rhs<NR>(U, w, cb, nrhs,
+                [&](int c, int j) { return v[(int64_t)c * n + Cidx[it.c0 + j]]; });
   __syncthreads();
-  double2* out = partial + blockIdx.y * pstride + it.part;
-  auto st = [=](int o, double2 y) { out[o] = y; };
-  if (!adjoint) mv_cols<false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, u, r, w, red, st);
-  else mv_dots<true>(B.XCR + it.c0, B.ldL, u, r, w, st);
+  auto st = [=](int o, int cc, double2 y) {
+    if (cb + cc < nrhs) partial[(int64_t)(cb + cc) * pstride + it.part + o] = y;
+  };
+  if (!adjoint) mvr_cols<NR, false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, U, w, r, w, red, st);
+  else mvr_dots<NR, true>(B.XCR + it.c0, B.ldL, U, w, r, w, st);
   int* ctr = cnt + (int64_t)it.box * gridDim.y + blockIdx.y;
   __threadfence();
   __syncthreads();
@@ -295,34 +437,37 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   // t[k] = sum_j partial_j[k]: threads over k (rp of them) and over
   // interleaved groups of j, four loads in flight each, groups summed in a
   // fixed order (the result does not depend on which CTA came last)
-  const double2* pb = partial + blockIdx.y * pstride + B.zoff;
-  double2* tb = partial + blockIdx.y * pstride + B.toff;
+  double2* redd = reinterpret_cast<double2*>(red);
   const int nc = B.item_cnt, t = threadIdx.x;
   const int rp = r <= 32 ? 32 : (r <= 64 ? 64 : (r <= 128 ? 128 : 256));
   const int G = 256 / rp, g = t / rp;
-  for (int kb = 0; kb < r; kb += rp) {
-    const int k = kb + t % rp;
-    double2 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
-    if (k < r) {
-      int j = g;
-      for (; j + 3 * G < nc; j += 4 * G) {
-        const double2 p0 = __ldcg(pb + (int64_t)j * r + k);
-        const double2 p1 = __ldcg(pb + (int64_t)(j + G) * r + k);
-        const double2 p2 = __ldcg(pb + (int64_t)(j + 2 * G) * r + k);
-        const double2 p3 = __ldcg(pb + (int64_t)(j + 3 * G) * r + k);
-        a0 = cadd(a0, cadd(p0, p2));
-        a1 = cadd(a1, cadd(p1, p3));
+  for (int cc = 0; cc < NR && cb + cc < nrhs; ++cc) {
+    const double2* pb = partial + (int64_t)(cb + cc) * pstride + B.zoff;
+    double2* tb = partial + (int64_t)(cb + cc) * pstride + B.toff;
+    for (int kb = 0; kb < r; kb += rp) {
+      const int k = kb + t % rp;
+      double2 a0 = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+      if (k < r) {
+        int j = g;
+        for (; j + 3 * G < nc; j += 4 * G) {
+          const double2 p0 = __ldcg(pb + (int64_t)j * r + k);
+          const double2 p1 = __ldcg(pb + (int64_t)(j + G) * r + k);
+          const double2 p2 = __ldcg(pb + (int64_t)(j + 2 * G) * r + k);
+          const double2 p3 = __ldcg(pb + (int64_t)(j + 3 * G) * r + k);
+          a0 = cadd(a0, cadd(p0, p2));
+          a1 = cadd(a1, cadd(p1, p3));
+        }
+        for (; j < nc; j += G) a0 = cadd(a0, __ldcg(pb + (int64_t)j * r + k));
       }
-      for (; j < nc; j += G) a0 = cadd(a0, __ldcg(pb + (int64_t)j * r + k));
+      redd[t] = cadd(a0, a1);
+      __syncthreads();
+      if (g == 0 && k < r) {
+        double2 sum = redd[t];
+        for (int gg = 1; gg < G; ++gg) sum = cadd(sum, redd[gg * rp + t]);
+        tb[k] = sum;
+      }
+      __syncthreads();
     }
-    red[t] = cadd(a0, a1);
-    __syncthreads();
-    if (g == 0 && k < r) {
-      double2 sum = red[t];
-      for (int gg = 1; gg < G; ++gg) sum = cadd(sum, red[gg * rp + t]);
-      tb[k] = sum;
-    }
-    __syncthreads();
   }
   if (t == 0) *ctr = 0;
 }
@@ -330,15 +475,25 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
 // The dynamic shared-memory limit is a per-device attribute of each kernel:
 // set it once per device (thread-safe), with that device current.
 constexpr int kSmemAttrDevices = 64;
+constexpr size_t kSweepSmemMax = 200 * 1024;
 static std::once_flag g_smem_attr_once[kSmemAttrDevices];
+
+template <int NR>
+static void set_smem_attr_nr() {
+  for (const void* f : {(const void*)k_sw_y<NR>, (const void*)k_sw_z<NR>,
+                        (const void*)k_sw_xr<NR>, (const void*)k_sw_xs<NR>,
+                        (const void*)k_fwd_c<NR>, (const void*)k_bwd_t<NR>})
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemMax);
+}
 
 static void set_smem_attr() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSmemAttrDevices) return;
   std::call_once(g_smem_attr_once[dev], [] {
-    for (const void* f : {(const void*)k_sw_y, (const void*)k_sw_z, (const void*)k_sw_xr,
-                          (const void*)k_sw_xs, (const void*)k_fwd_c, (const void*)k_bwd_t})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set_smem_attr_nr<1>();
+    set_smem_attr_nr<2>();
+    set_smem_attr_nr<4>();
+    set_smem_attr_nr<8>();
   });
 }
 
@@ -362,38 +517,65 @@ void launch_copy_z(const SolveBox* boxes, int b0, int nb, int rmax, double2* v, 
                k_copy_z<<<dim3(nb, nrhs), th, 0, st>>>(boxes, b0, v, n, partial, pstride));
 }
 
+template <int NR>
+static void launch_sweep_nr(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
+                            double2* v, int64_t n, int nrhs, bool backward, int adj,
+                            double2* partial, int64_t pstride, cudaStream_t st, int* cnt,
+                            bool skip_c) {
+  const unsigned ng = (unsigned)((nrhs + NR - 1) / NR);
+  const size_t red = 256 * sizeof(float4);
+  const size_t smr = red + (size_t)NR * sg.rmax * sizeof(float4);
+  if (!backward) {
+    if (sg.smax > 0)
+      FMMLU_LAUNCH("sweep_fwd", st,
+                   k_sw_y<NR><<<dim3(sg.nri, ng), 256, (size_t)NR * sg.smax * sizeof(float4), st>>>(
+                       boxes, items, sg.ri0, v, n, nrhs, adj));
+    FMMLU_LAUNCH("sweep_fwd", st,
+                 k_sw_z<NR><<<dim3(sg.nri, ng), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
+                                                                partial, pstride, nrhs, adj));
+    if (!skip_c)
+      FMMLU_LAUNCH("sweep_fwd_c", st,
+                   k_fwd_c<NR><<<dim3(sg.ni, ng), 256, smr, st>>>(boxes, items, sg.i0, v, n,
+                                                                  partial, pstride, nrhs, adj));
+  } else {
+    const size_t sm1 = red + (size_t)NR * sg.chunk * sizeof(float4);
+    if (!skip_c)
+      FMMLU_LAUNCH("sweep_bwd_t", st,
+                   k_bwd_t<NR><<<dim3(sg.ni, ng), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
+                                                                    partial, pstride, cnt, nrhs,
+                                                                    adj));
+    FMMLU_LAUNCH("sweep_bwd", st,
+                 k_sw_xr<NR><<<dim3(sg.nri, ng), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
+                                                                 partial, pstride, nrhs, adj));
+    if (sg.nsi > 0)
+      FMMLU_LAUNCH("sweep_bwd", st,
+                   k_sw_xs<NR><<<dim3(sg.nsi, ng), 256, smr, st>>>(boxes, items, sg.si0, v, n,
+                                                                   nrhs, adj));
+  }
+}
+
+static int sweep_group_size(int nrhs, int qmax) {
+  // the largest group (at most 8, at most the next power of two above nrhs)
+  // whose staged right-hand sides and reduction buffer fit in shared memory
+  int nr = 8;
+  while (nr > 1 && (nr / 2 >= nrhs || 256 * sizeof(float4) + (size_t)nr * qmax * sizeof(float4) >
+                                          kSweepSmemMax))
+    nr >>= 1;
+  return nr;
+}
+
 void launch_sweep(const SolveBox* boxes, const SweepItem* items, const SweepSeg& sg,
                   double2* v, int64_t n, int nrhs, bool backward, bool adjoint,
                   double2* partial, int64_t pstride, cudaStream_t st, int* cnt, bool skip_c) {
   if (sg.nb <= 0) return;
   set_smem_attr();
   const int adj = adjoint ? 1 : 0;
-  const size_t red = 256 * sizeof(double2);
-  const size_t smr = red + (size_t)sg.rmax * sizeof(double2);
-  if (!backward) {
-    if (sg.smax > 0)
-      FMMLU_LAUNCH("sweep_fwd", st,
-                   k_sw_y<<<dim3(sg.nri, nrhs), 256, (size_t)sg.smax * sizeof(double2), st>>>(
-                       boxes, items, sg.ri0, v, n, adj));
-    FMMLU_LAUNCH("sweep_fwd", st,
-                 k_sw_z<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
-                                                             partial, pstride, adj));
-    if (!skip_c)
-      FMMLU_LAUNCH("sweep_fwd_c", st,
-                   k_fwd_c<<<dim3(sg.ni, nrhs), 256, smr, st>>>(boxes, items, sg.i0, v, n,
-                                                               partial, pstride, adj));
-  } else {
-    const size_t sm1 = red + (size_t)sg.chunk * sizeof(double2);
-    if (!skip_c)
-      FMMLU_LAUNCH("sweep_bwd_t", st,
-                   k_bwd_t<<<dim3(sg.ni, nrhs), 256, sm1, st>>>(boxes, items, sg.i0, v, n,
-                                                                 partial, pstride, cnt, adj));
-    FMMLU_LAUNCH("sweep_bwd", st,
-                 k_sw_xr<<<dim3(sg.nri, nrhs), 256, smr, st>>>(boxes, items, sg.ri0, v, n,
-                                                              partial, pstride, adj));
-    if (sg.nsi > 0)
-      FMMLU_LAUNCH("sweep_bwd", st,
-                   k_sw_xs<<<dim3(sg.nsi, nrhs), 256, smr, st>>>(boxes, items, sg.si0, v, n, adj));
+  const int nr = sweep_group_size(nrhs, std::max(std::max(sg.rmax, sg.smax), sg.chunk));
+  switch (nr) {
+    case 8: launch_sweep_nr<8>(boxes, items, sg, v, n, nrhs, backward, adj, partial, pstride, st, cnt, skip_c); break;
+    case 4: launch_sweep_nr<4>(boxes, items, sg, v, n, nrhs, backward, adj, partial, pstride, st, cnt, skip_c); break;
+    case 2: launch_sweep_nr<2>(boxes, items, sg, v, n, nrhs, backward, adj, partial, pstride, st, cnt, skip_c); break;
+    default: launch_sweep_nr<1>(boxes, items, sg, v, n, nrhs, backward, adj, partial, pstride, st, cnt, skip_c); break;
   }
 }
 
