@@ -160,7 +160,8 @@ __device__ __forceinline__ void mv_dots(const double2* __restrict__ M, int64_t l
 // is the contiguous one. 256 threads: consecutive threads take consecutive
 // outputs (16 or 32 per tile); when fewer than 256 outputs are left, the
 // remaining threads split q into interleaved groups whose sums meet in red
-// (256 entries, one right-hand side at a time, in a fixed group order).
+// (256 entries per right-hand side, summed in a fixed group order).
+// store(o, y) receives the NR results of output o.
 template <int NR, bool kCj, class Store>
 __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t ld,
                                          const float4* X, int xs, int no, int nq, float4* red,
@@ -192,26 +193,32 @@ __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t 
       }
       if (q < nq) apply(Mo[(int64_t)q * ld], q);
     }
+    double2 y[NR];
     if (qg == 1) {
-      if (o < no)
+      if (o < no) {
 #pragma unroll
-        for (int cc = 0; cc < NR; ++cc) store(o, cc, make_double2(df_value(ar[cc]), df_value(ai[cc])));
+        for (int cc = 0; cc < NR; ++cc) y[cc] = make_double2(df_value(ar[cc]), df_value(ai[cc]));
+        store(o, y);
+      }
     } else {
 #pragma unroll
-      for (int cc = 0; cc < NR; ++cc) {
-        red[t] = make_float4(ar[cc].h, ar[cc].l, ai[cc].h, ai[cc].l);
-        __syncthreads();
-        if (g == 0 && o < no) {
+      for (int cc = 0; cc < NR; ++cc)
+        red[cc * 256 + t] = make_float4(ar[cc].h, ar[cc].l, ai[cc].h, ai[cc].l);
+      __syncthreads();
+      if (g == 0 && o < no) {
+#pragma unroll
+        for (int cc = 0; cc < NR; ++cc) {
           DF sr = ar[cc], si = ai[cc];
           for (int gg = 1; gg < qg; ++gg) {
-            const float4 w = red[gg * span + oi];
+            const float4 w = red[cc * 256 + gg * span + oi];
             sr = df_add(sr, DF{w.x, w.y});
             si = df_add(si, DF{w.z, w.w});
           }
-          store(o, cc, make_double2(df_value(sr), df_value(si)));
+          y[cc] = make_double2(df_value(sr), df_value(si));
         }
-        __syncthreads();
+        store(o, y);
       }
+      __syncthreads();
     }
   }
 }
@@ -247,11 +254,13 @@ __device__ __forceinline__ void mvr_dots(const double2* __restrict__ M, int64_t 
       }
       if (q < nq) apply(Mo[q], q);
     }
+    double2 y[NR];
 #pragma unroll
     for (int cc = 0; cc < NR; ++cc) {
       const DF sr = df_group_sum(ar[cc], sw), si = df_group_sum(ai[cc], sw);
-      if (sl == 0 && o < no) store(o, cc, make_double2(df_value(sr), df_value(si)));
+      y[cc] = make_double2(df_value(sr), df_value(si));
     }
+    if (sl == 0 && o < no) store(o, y);
   }
 }
 
@@ -263,6 +272,20 @@ __device__ __forceinline__ void stage_rhs(float4* X, int cnt, int cb, int nrhs, 
     const int cc = e / cnt, k = e - cc * cnt;
     X[e] = cb + cc < nrhs ? cdf_split_bits(load(cb + cc, k)) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+
+// v[c][dof] -= y[cc] for the group's right-hand sides (all old values are
+// read before any is written back)
+template <int NR>
+__device__ __forceinline__ void sub_rhs(double2* v, int64_t n, int cb, int nrhs, int dof,
+                                        const double2* y) {
+  double2 old[NR];
+#pragma unroll
+  for (int cc = 0; cc < NR; ++cc)
+    if (cb + cc < nrhs) old[cc] = v[(int64_t)(cb + cc) * n + dof];
+#pragma unroll
+  for (int cc = 0; cc < NR; ++cc)
+    if (cb + cc < nrhs) v[(int64_t)(cb + cc) * n + dof] = csub(old[cc], y[cc]);
 }
 
 // forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
@@ -281,11 +304,7 @@ __global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes
   __syncthreads();
   const int kc = it.c1 - it.c0;
   const int* Ridx = B.idx + it.c0;
-  auto st = [=](int o, int cc, double2 y) {
-    if (cb + cc >= nrhs) return;
-    double2* p = v + (int64_t)(cb + cc) * n + Ridx[o];
-    *p = csub(*p, y);
-  };
+  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Ridx[o], y); };
   const double2* M = B.T + (int64_t)it.c0 * B.ldT;
   if (adjoint) mvr_dots<NR, true>(M, B.ldT, X, B.s, kc, B.s, st);
   else mvr_dots<NR, false>(M, B.ldT, X, B.s, kc, B.s, st);
@@ -310,13 +329,15 @@ __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int cb = blockIdx.y * NR;
-  float4* red = shf;
-  float4* Y = shf + 256;        // NR x r
+  float4* red = shf;            // NR x 256
+  float4* Y = shf + NR * 256;   // NR x r
   stage_rhs<NR>(Y, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
   double2* zo = zbuf + B.zoff + it.c0;
-  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Y, red, adjoint != 0, [=](int o, int cc, double2 z) {
-    if (cb + cc < nrhs) zo[(int64_t)(cb + cc) * zstride + o] = z;
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Y, red, adjoint != 0, [=](int o, const double2* z) {
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc)
+      if (cb + cc < nrhs) zo[(int64_t)(cb + cc) * zstride + o] = z[cc];
   });
 }
 
@@ -331,16 +352,14 @@ __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxe
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int cb = blockIdx.y * NR;
-  float4* red = shf;
-  float4* Tt = shf + 256;       // NR x r
+  float4* red = shf;            // NR x 256
+  float4* Tt = shf + NR * 256;  // NR x r
   stage_rhs<NR>(Tt, B.r, cb, nrhs,
                 [&](int c, int k) { return partial[(int64_t)c * pstride + B.toff + k]; });
   __syncthreads();
   const int* Ridx = B.idx + it.c0;
-  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Tt, red, adjoint != 0, [=](int o, int cc, double2 y) {
-    if (cb + cc >= nrhs) return;
-    double2* p = v + (int64_t)(cb + cc) * n + Ridx[o];
-    *p = csub(*p, y);
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Tt, red, adjoint != 0, [=](int o, const double2* y) {
+    sub_rhs<NR>(v, n, cb, nrhs, Ridx[o], y);
   });
 }
 
@@ -354,16 +373,12 @@ __global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxe
   const SweepItem it = items[i0 + blockIdx.x];
   const SolveBox B = boxes[it.box];
   const int cb = blockIdx.y * NR;
-  float4* red = shf;
-  float4* Xr = shf + 256;       // NR x r
+  float4* red = shf;            // NR x 256
+  float4* Xr = shf + NR * 256;  // NR x r
   stage_rhs<NR>(Xr, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
   const int* Sidx = B.idx + B.r + it.c0;
-  auto st = [=](int o, int cc, double2 y) {
-    if (cb + cc >= nrhs) return;
-    double2* p = v + (int64_t)(cb + cc) * n + Sidx[o];
-    *p = csub(*p, y);
-  };
+  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Sidx[o], y); };
   if (adjoint) mvr_cols<NR, true>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
   else mvr_cols<NR, false>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
 }
@@ -380,8 +395,8 @@ __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxe
   const SolveBox B = boxes[it.box];
   const int r = B.r;
   const int cb = blockIdx.y * NR;
-  float4* red = shf;
-  float4* Z = shf + 256;        // NR x r
+  float4* red = shf;            // NR x 256
+  float4* Z = shf + NR * 256;   // NR x r
   stage_rhs<NR>(Z, r, cb, nrhs, [&](int c, int k) {
     const double2 zv = zbuf[(int64_t)c * zstride + B.zoff + k];
     if (it.c0 == 0) v[(int64_t)c * n + B.idx[k]] = zv;   // b_R = z, once per box
@@ -389,11 +404,7 @@ __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxe
   });
   __syncthreads();
   const int* Cidx = B.idx + r + it.c0;
-  auto st = [=](int o, int cc, double2 y) {
-    if (cb + cc >= nrhs) return;
-    double2* p = v + (int64_t)(cb + cc) * n + Cidx[o];
-    *p = csub(*p, y);
-  };
+  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Cidx[o], y); };
   const int w = it.c1 - it.c0;
   if (!adjoint) mvr_cols<NR, false>(B.XCR + it.c0, B.ldL, Z, r, w, r, red, st);
   else mvr_dots<NR, true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, Z, r, w, r, st);
@@ -416,14 +427,16 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   const int r = B.r;
   const int cb = blockIdx.y * NR;
   const int w = it.c1 - it.c0;
-  float4* red = shf;            // 256
-  float4* U = shf + 256;        // NR x w: the chunk's values of x_C
+  float4* red = shf;            // NR x 256
+  float4* U = shf + NR * 256;   // NR x w: the chunk's values of x_C
   const int* Cidx = B.idx + r;
   stage_rhs<NR>(U, w, cb, nrhs,
                 [&](int c, int j) { return v[(int64_t)c * n + Cidx[it.c0 + j]]; });
   __syncthreads();
-  auto st = [=](int o, int cc, double2 y) {
-    if (cb + cc < nrhs) partial[(int64_t)(cb + cc) * pstride + it.part + o] = y;
+  auto st = [=](int o, const double2* y) {
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc)
+      if (cb + cc < nrhs) partial[(int64_t)(cb + cc) * pstride + it.part + o] = y[cc];
   };
   if (!adjoint) mvr_cols<NR, false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, U, w, r, w, red, st);
   else mvr_dots<NR, true>(B.XCR + it.c0, B.ldL, U, w, r, w, st);
@@ -523,7 +536,7 @@ static void launch_sweep_nr(const SolveBox* boxes, const SweepItem* items, const
                             double2* partial, int64_t pstride, cudaStream_t st, int* cnt,
                             bool skip_c) {
   const unsigned ng = (unsigned)((nrhs + NR - 1) / NR);
-  const size_t red = 256 * sizeof(float4);
+  const size_t red = (size_t)NR * 256 * sizeof(float4);
   const size_t smr = red + (size_t)NR * sg.rmax * sizeof(float4);
   if (!backward) {
     if (sg.smax > 0)
@@ -558,8 +571,7 @@ static int sweep_group_size(int nrhs, int qmax) {
   // the largest group (at most 8, at most the next power of two above nrhs)
   // whose staged right-hand sides and reduction buffer fit in shared memory
   int nr = 8;
-  while (nr > 1 && (nr / 2 >= nrhs || 256 * sizeof(float4) + (size_t)nr * qmax * sizeof(float4) >
-                                          kSweepSmemMax))
+  while (nr > 1 && (nr / 2 >= nrhs || (size_t)nr * (256 + qmax) * sizeof(float4) > kSweepSmemMax))
     nr >>= 1;
   return nr;
 }

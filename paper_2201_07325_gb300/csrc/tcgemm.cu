@@ -44,6 +44,11 @@ constexpr int kThreads = 320;
 constexpr int kRows = 128;                      // tile rows (MMA M)
 constexpr int kCols = 32;                       // complex tile columns (MMA N = 64)
 constexpr int kAChunk = kRows * 16 * 2;         // one digit part of A, one k16 step
+// 8-row groups stored per k-half of an A chunk: an operand with at most 128
+// rows keeps only its own rows (the MMA still reads 128; the rows past the
+// operand hold other data and give output rows that are never stored)
+__host__ __device__ __forceinline__ int a_groups(int m) { return m <= kRows ? (m + 7) / 8 : kRows / 8; }
+__host__ __device__ __forceinline__ int a_chunk(int m) { return a_groups(m) * 256; }
 constexpr int kBChunk = 3 * kCols * 16 * 2;     // one digit of B (three parts)
 constexpr long long kWaitLimit = 20000000;      // polls (~1-2 s)
 
@@ -659,10 +664,11 @@ __device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
     tc::balanced_digits<NS>(v.y, e, ci[u]);
   }
   const int ks = ko >> 1, kc = ko & 1;
-  if (!SideB) {
+  const int ga = tc::a_groups(m), ach = tc::a_chunk(m);
+  if (!SideB && (row % tc::kRows) < 8 * ga) {
     const int blk = row / tc::kRows, r = row % tc::kRows;
-    unsigned char* step = slices + t.a_off + ((int64_t)blk * KS + ks) * (2 * NS) * tc::kAChunk;
-    const int off = (kc * (tc::kRows / 8) + (r >> 3)) * 128 + (r & 7) * 16;
+    unsigned char* step = slices + t.a_off + ((int64_t)blk * KS + ks) * (2 * NS) * ach;
+    const int off = (kc * ga + (r >> 3)) * 128 + (r & 7) * 16;
 #pragma unroll
     for (int p = 0; p < NS; ++p) {
       uint4 vr, vi;
@@ -670,8 +676,8 @@ __device__ __forceinline__ void tc_digits_unit(const LevelDev& L, int b0,
       vr.z = pack_bf16x2(cr[4][p], cr[5][p]); vr.w = pack_bf16x2(cr[6][p], cr[7][p]);
       vi.x = pack_bf16x2(ci[0][p], ci[1][p]); vi.y = pack_bf16x2(ci[2][p], ci[3][p]);
       vi.z = pack_bf16x2(ci[4][p], ci[5][p]); vi.w = pack_bf16x2(ci[6][p], ci[7][p]);
-      *reinterpret_cast<uint4*>(step + (2 * p) * tc::kAChunk + off) = vr;
-      *reinterpret_cast<uint4*>(step + (2 * p + 1) * tc::kAChunk + off) = vi;
+      *reinterpret_cast<uint4*>(step + (2 * p) * ach + off) = vr;
+      *reinterpret_cast<uint4*>(step + (2 * p + 1) * ach + off) = vi;
     }
   }
   // The Gram product's B operand is M itself: column j of B is row j of A
@@ -805,14 +811,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
         if (!T.ok) continue;
         const TcBoxHost t = tb[T.rel];
-        const unsigned char* srcA = slices + t.a_off + ((int64_t)T.tm * T.KSall + T.k0) * kA;
+        const int kAt = NS * 2 * a_chunk(T.m);   // this tile's A bytes per k16 step
+        const unsigned char* srcA = slices + t.a_off + ((int64_t)T.tm * T.KSall + T.k0) * kAt;
         const unsigned char* srcB = slices + t.b_off + ((int64_t)T.tn * T.KSall + T.k0) * kB;
         for (int ks = 0; ks < T.KS; ++ks, ++g) {
           const int s = g & 1;
           if (g >= 2 && !mbar_wait(&bar_empty[s], ((g >> 1) - 1) & 1, abort_flag)) { ok = false; break; }
           unsigned char* st = sm + s * kStage;
-          mbar_expect_tx(&bar_full[s], (uint32_t)kStage);
-          bulk_g2s(st, srcA + (int64_t)ks * kA, (uint32_t)kA, &bar_full[s]);
+          mbar_expect_tx(&bar_full[s], (uint32_t)(kAt + kB));
+          bulk_g2s(st, srcA + (int64_t)ks * kAt, (uint32_t)kAt, &bar_full[s]);
           bulk_g2s(st + kA, srcB + (int64_t)ks * kB, (uint32_t)kB, &bar_full[s]);
         }
       }
@@ -829,7 +836,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       const uint32_t smem0 = su32(sm);
       const uint32_t boffA = Prob::kConj ? 0u : 512u;   // B rows for the A_re product
       const uint32_t boffB = Prob::kConj ? 512u : 0u;   // B rows for the A_im product
-      const uint64_t dA = sdesc(0, 2048, 128), dB = sdesc(0, 1536, 128);
+      const uint64_t dB = sdesc(0, 1536, 128);
       // per accumulator: bit d of `opened` = a window of d was opened before,
       // bit d of `wpar` = parity of the number of windows of d opened
       uint32_t opened = 0, wpar = 0;
@@ -838,6 +845,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       for (int ui = blockIdx.x; ui < nunits && ok; ui += gridDim.x) {
         const TcTile T = tc_tile<Prob>(L, b0, units[ui]);
         if (!T.ok) continue;
+        const int ach = a_chunk(T.m);
+        const uint64_t dA = sdesc(0, (uint32_t)(a_groups(T.m) * 128), 128);
         for (int ks = 0; ks < T.KS && ok; ++ks, ++g) {
           const int s = g & 1;
           if (!mbar_wait(&bar_full[s], (g >> 1) & 1, abort_flag)) { ok = false; break; }
@@ -857,7 +866,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             uint32_t acc = start ? 0u : 1u;
             for (int p = plo(dd, NS); p <= phi(dd, NS); ++p) {
               const int q = dd - p;
-              const uint32_t ar = aS + (2 * p) * kAChunk, ai = ar + kAChunk;
+              const uint32_t ar = aS + (2 * p) * ach, ai = ar + ach;
               const uint32_t bq = bS + q * kBChunk;
               mma(dt, dA + (ar >> 4), dB + ((bq + boffA) >> 4), acc);
               mma(dt, dA + (ai >> 4), dB + ((bq + boffB) >> 4), 1u);
