@@ -172,7 +172,29 @@ struct ScratchPool {
   }
 };
 
-inline void cudaFreeHost_void(BoxRun* p) { if (p) cudaFreeHost(p); }
+// Pinned host buffers in numbered slots, grown (never shrunk) on demand.
+struct PinnedPool {
+  std::vector<std::pair<void*, size_t>> slots;
+  template <typename T>
+  T* get(int slot, size_t count) {
+    if ((int)slots.size() <= slot) slots.resize((size_t)slot + 1, {nullptr, 0});
+    auto& sl = slots[(size_t)slot];
+    const size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+    if (sl.second < bytes) {
+      if (sl.first) cudaFreeHost(sl.first);
+      sl.first = nullptr;
+      sl.second = 0;
+      CK(cudaMallocHost(&sl.first, bytes));
+      sl.second = bytes;
+    }
+    return static_cast<T*>(sl.first);
+  }
+  ~PinnedPool() {
+    for (auto& sl : slots)
+      if (sl.first) cudaFreeHost(sl.first);
+  }
+};
+
 
 // A unit list of tcgen05 launches: pinned host staging and its device copy.
 // The staging buffer is rewritten only after the previous copy out of it has
@@ -908,6 +930,25 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   } ev_run_holder;
   CK(cudaEventCreateWithFlags(&ev_run_holder.e, cudaEventDisableTiming));
   cudaEvent_t ev_run = ev_run_holder.e;
+  // Pinned host buffers reused from level to level (grown, never shrunk):
+  // a level's box ranks, its final active counts and positions (read by the
+  // host as soon as the last colour's IDs are done, while the GPU still runs
+  // that colour's products and the host sets up the next level), and its
+  // status word and refinement residuals (read one level later, once the
+  // GPU has finished the level).
+  PinnedPool pinned;
+  enum { kPinRun = 0, kPinCurN = 1, kPinActPos = 2, kPinStatus = 3, kPinNs = 4, kPinStatusIds = 5 };
+  Ev ev_ids_holder;   // the last colour's IDs of a level are final
+  CK(cudaEventCreateWithFlags(&ev_ids_holder.e, cudaEventDisableTiming));
+  cudaEvent_t ev_ids = ev_ids_holder.e;
+  // a level whose status and statistics are read once its GPU work is done
+  struct Pending {
+    bool on = false;
+    int lev = 0, nb = 0, colours = 0, nprox = 0, ns_rmax = 0;
+    size_t current = 0;
+    int64_t sum_a = 0, sum_s = 0, max_a = 0, max_r = 0, pool = 0;
+    std::vector<int> r;                 // per box
+  } pend;
   H->d_perm = H->mem.get<int>((size_t)n);
   CK(cudaMemcpyAsync(H->d_perm, tree->d_perm, n * sizeof(int), cudaMemcpyDeviceToDevice, st));
   double* soa = work.get<double>((size_t)n * 8);
@@ -927,18 +968,60 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   std::unique_ptr<LevelState> prev;
   int root_level = 1;
   bool first_level = true;
+  // events around each level's GPU work, alternating by level parity (a
+  // level's pair is read while the next level runs)
+  Ev lev_t0[2], lev_t1[2];
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaEventCreate(&lev_t0[q].e));
+    CK(cudaEventCreate(&lev_t1[q].e));
+  }
+  // the previous level's status word, refinement statistics and stats entry;
+  // called after a stream synchronisation, when that level's work is done
+  auto finish_pending = [&]() {
+    if (!pend.on) return;
+    pend.on = false;
+    const int status = *pinned.get<int>(kPinStatus, 1);
+    std::string msg;
+    if (int code = status_to_code(status, msg))
+      throw Error(code, msg + " (level " + std::to_string(pend.lev) + ")");
+    int ns_boxes = 0, ns_fallback = 0;
+    double ns_worst = 0.0;
+    if (pend.ns_rmax >= kNsMin) {
+      const unsigned long long* errs = pinned.get<unsigned long long>(kPinNs, (size_t)pend.nb);
+      for (int e = 0; e < pend.nb; ++e) {
+        if (pend.r[e] < kNsMin || pend.r[e] > pend.ns_rmax) continue;
+        double v;
+        std::memcpy(&v, &errs[e], sizeof(v));
+        ++ns_boxes;
+        ns_worst = std::max(ns_worst, v);
+        if (!(v <= opt.xrr_refine_tol)) ++ns_fallback;
+      }
+    }
+    float lms = 0.f;
+    CK(cudaEventElapsedTime(&lms, lev_t0[pend.lev & 1].e, lev_t1[pend.lev & 1].e));
+    if (opt.verbose)
+      std::fprintf(stderr, "[fmmlu] level %d: boxes %d colours %d current %zu sum_a %lld sum_s %lld max_a %lld max_r %lld pool %.1f MB %.1f ms; refined inverses %d (worst residual %.1e, fp64 again %d)\n",
+                   pend.lev, pend.nb, pend.colours, pend.current, (long long)pend.sum_a,
+                   (long long)pend.sum_s, (long long)pend.max_a, (long long)pend.max_r,
+                   pend.pool * 16.0 / 1e6, (double)lms, ns_boxes, ns_worst, ns_fallback);
+    js << (first_level ? "" : ", ") << "{\"level\": " << pend.lev << ", \"boxes\": " << pend.nb
+       << ", \"colours\": " << pend.colours << ", \"n_proxy\": " << pend.nprox
+       << ", \"current\": " << pend.current
+       << ", \"sum_a\": " << pend.sum_a << ", \"sum_s\": " << pend.sum_s << ", \"max_a\": " << pend.max_a
+       << ", \"max_r\": " << pend.max_r << ", \"refined_inverses\": " << ns_boxes
+       << ", \"refine_fallbacks\": " << ns_fallback << ", \"ms\": " << lms << "}";
+    first_level = false;
+  };
   for (int lev = T.nlevels - 1; lev >= 2; --lev) {
-    Timer lt;
     const HLevel& HL = T.levels.at(lev);
+    CK(cudaEventRecord(lev_t0[lev & 1].e, st));
     std::unique_ptr<LevelState> L;
     {
       HostTimer mt(&HostTimes::make_level);
       L = make_level(T, lev, prev.get(), &HL, st);
     }
-    stream_wait(st);   // the merge has read the previous level
     const auto setup0 = std::chrono::steady_clock::now();
     auto sub0 = setup0;
-    prev.reset();
     // stop rule: any level box with active far DOFs?
     const int nb = (int)HL.boxes.size();
     bool far_any = false;
@@ -1054,12 +1137,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     LevelDev LD;
     LD.desc = lw.up(desc, st);
     BoxRun* d_run = lw.get<BoxRun>((size_t)nb);
-    std::unique_ptr<BoxRun, decltype(&cudaFreeHost_void)> h_run_owner(nullptr, &cudaFreeHost_void);
-    BoxRun* h_run = nullptr;
-    if (opt.schur_emulation == 1) {
-      CK(cudaMallocHost(&h_run, (size_t)std::max(nb, 1) * sizeof(BoxRun)));
-      h_run_owner.reset(h_run);
-    }
+    BoxRun* h_run = opt.schur_emulation == 1 ? pinned.get<BoxRun>(kPinRun, (size_t)nb) : nullptr;
     CK(cudaMemsetAsync(d_run, 0, nb * sizeof(BoxRun), st));
     LD.run = d_run;
     LD.nlist = lw.up(nlist, st);
@@ -1084,6 +1162,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     // refinement of X_RR^{-1} (tcgen05 path): per colour an X_RR copy and a
     // product scratch of a^2 each per box
     int ns_rmax = 0;
+    unsigned char* d_ns_skip = nullptr;   // boxes that skip the third refinement step
     if (opt.schur_emulation == 1 && opt.xrr_refine_tol >= 0.0) {   // the tcgen05 path
       for (int r = kNsMin; r <= 4096; r += 8)
         if (gj32_cluster_size(r) > 0) ns_rmax = r; else break;
@@ -1103,6 +1182,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       LD.nsbuf = ns_rmax >= kNsMin ? lw.get<double2>((size_t)ns_max) : nullptr;
       LD.ns_off = lw.up(nso, st);
       LD.ns_err = lw.get<unsigned long long>((size_t)nb);
+      d_ns_skip = lw.get<unsigned char>((size_t)nb);
       LD.ns_rmax = ns_rmax;
     }
     // CPQR plan per colour: boxes share the co-resident CTAs in proportion to
@@ -1330,6 +1410,11 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     unsigned char* d_gj_scratch = lw.get<unsigned char>((size_t)gj_scratch);
     ht.setup += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
                                                           setup0).count();
+    // the set-up above ran on the host while the GPU finished the previous
+    // level and merged its Schur blocks into this level's pool
+    stream_wait(st);
+    prev.reset();
+    finish_pending();
     for (size_t sgi = 0; sgi + 1 < seg_start.size(); ++sgi) {
       int b0 = seg_start[sgi], cnt = seg_start[sgi + 1] - b0;
       int amax = 1, mmax = 1, nmaxm = 0;
@@ -1383,6 +1468,17 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
       if (use_tc) {
         CK(cudaMemcpyAsync(h_run + b0, d_run + b0, cnt * sizeof(BoxRun), cudaMemcpyDeviceToHost,
                            st));
+        if (sgi + 2 == seg_start.size()) {
+          // the last colour's IDs complete the level's active counts and
+          // positions: copy them now, ahead of the colour's products
+          CK(cudaMemcpyAsync(pinned.get<int>(kPinCurN, L->cur.size()), L->d_cur_n,
+                             L->cur.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+          CK(cudaMemcpyAsync(pinned.get<int>(kPinActPos, L->act_pos.size()), L->d_act_pos,
+                             L->act_pos.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+          CK(cudaMemcpyAsync(pinned.get<int>(kPinStatusIds, 1), d_status, sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+          CK(cudaEventRecord(ev_ids, st));
+        }
         CK(cudaEventRecord(ev_run, st));
       }
       // the elimination blocks need no plan: the GPU assembles them while the
@@ -1453,15 +1549,26 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
             launch_tc_planned(w, LD, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr, false,
                               elim_units.d, epl[w], st);
           };
-          // three steps; the last product's residual e bounds the result's
-          // by (r e)^2, so e <= 1e-9 leaves it below ~1e-12 for r <= 640
-          ns(kTcNsY);
-          ns(kTcNsX);
+          // up to three steps. A step's residual e (max |I - X_RR X|) bounds
+          // the next iterate's by (r e)^2: boxes whose second-step residual
+          // gives (r e)^2 <= min(tol, eps / 100) skip the third step; for the
+          // others the third step's residual must be <= tol, leaving the
+          // result below ~1e-12 for r <= 640 (else fp64 Gauss-Jordan again)
           ns(kTcNsY);
           ns(kTcNsX);
           CK(cudaMemsetAsync(LD.ns_err + b0, 0, (size_t)cnt * sizeof(unsigned long long), st));
           ns(kTcNsY);
           ns(kTcNsX);
+          launch_ns_flag(LD, b0, elim_units.d + ns_off0, ns_cnt,
+                         std::min(opt.xrr_refine_tol, 1e-2 * eps), d_ns_skip, st);
+          {
+            LevelDev LD3 = LD;
+            LD3.ns_skip = d_ns_skip;
+            launch_tc_planned(kTcNsY, LD3, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                              false, elim_units.d, epl[kTcNsY], st);
+            launch_tc_planned(kTcNsX, LD3, b0, d_tcb + b0, d_tc_slices, d_tc_expo, nullptr, nullptr,
+                              false, elim_units.d, epl[kTcNsX], st);
+          }
           launch_ns_fallback(LD, b0, elim_units.d + ns_off0, ns_cnt, amax, opt.xrr_refine_tol, st);
           ns_done = true;
         } else if (eg != cudaErrorNotSupported) {
@@ -1490,12 +1597,42 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         launch_oz_schur(LD, b0, cnt, d_ozb + b0, d_oz_slices, d_oz_expo, amax, nmaxm, st);
       CK(cudaGetLastError());
     }
-    std::vector<BoxRun> run = ddownload(d_run, (size_t)nb, st);
-    int status = ddownload(d_status, 1, st)[0];
-    std::string msg;
-    if (int code = status_to_code(status, msg)) throw Error(code, msg + " (level " + std::to_string(lev) + ")");
-    L->cur_n = ddownload(L->d_cur_n, L->cur.size(), st);
-    L->act_pos = ddownload(L->d_act_pos, L->act_pos.size(), st);
+    std::vector<BoxRun> run;
+    int* h_status = pinned.get<int>(kPinStatus, 1);
+    if (use_tc) {
+      // counts and positions as copied after the last colour's IDs; the GPU
+      // may still run that colour's products. The status word and the
+      // refinement residuals are read with the next level.
+      {
+        HostTimer wt(&HostTimes::wait);
+        CK(cudaEventSynchronize(ev_ids));
+      }
+      std::string msg;   // the IDs must have succeeded before their ranks are used
+      if (int code = status_to_code(*pinned.get<int>(kPinStatusIds, 1), msg))
+        throw Error(code, msg + " (level " + std::to_string(lev) + ")");
+      run.assign(h_run, h_run + nb);
+      const int* pcn = pinned.get<int>(kPinCurN, L->cur.size());
+      const int* pap = pinned.get<int>(kPinActPos, L->act_pos.size());
+      L->cur_n.assign(pcn, pcn + L->cur.size());
+      L->act_pos.assign(pap, pap + L->act_pos.size());
+      CK(cudaMemcpyAsync(h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (ns_rmax >= kNsMin)
+        CK(cudaMemcpyAsync(pinned.get<unsigned long long>(kPinNs, (size_t)nb), LD.ns_err,
+                           (size_t)nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    } else {
+      run = ddownload(d_run, (size_t)nb, st);
+      *h_status = ddownload(d_status, 1, st)[0];
+      std::string msg;
+      if (int code = status_to_code(*h_status, msg))
+        throw Error(code, msg + " (level " + std::to_string(lev) + ")");
+      L->cur_n = ddownload(L->d_cur_n, L->cur.size(), st);
+      L->act_pos = ddownload(L->d_act_pos, L->act_pos.size(), st);
+      if (ns_rmax >= kNsMin) {
+        std::vector<unsigned long long> errs = ddownload(LD.ns_err, (size_t)nb, st);
+        std::memcpy(pinned.get<unsigned long long>(kPinNs, (size_t)nb), errs.data(),
+                    (size_t)nb * sizeof(unsigned long long));
+      }
+    }
     if (H->profile) {
       H->prof.resolve();
       const double csz = H->fp32 ? 8.0 : 16.0;
@@ -1614,35 +1751,25 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
         H->sseg.push_back(sg);
       }
     }
-    double lms = lt.ms();
-    // refinement of X_RR^{-1}: boxes refined, largest final-step residual, fallbacks
-    int ns_boxes = 0, ns_fallback = 0;
-    double ns_worst = 0.0;
-    if (ns_rmax >= kNsMin) {
-      std::vector<unsigned long long> errs = ddownload(LD.ns_err, (size_t)nb, st);
-      for (int e = 0; e < nb; ++e) {
-        if (run[e].r < kNsMin || run[e].r > ns_rmax) continue;
-        double v;
-        std::memcpy(&v, &errs[e], sizeof(v));
-        ++ns_boxes;
-        ns_worst = std::max(ns_worst, v);
-        if (!(v <= opt.xrr_refine_tol)) ++ns_fallback;
-      }
-    }
-    if (opt.verbose)
-      std::fprintf(stderr, "[fmmlu] level %d: boxes %d colours %d current %zu sum_a %lld sum_s %lld max_a %lld max_r %lld pool %.1f MB %.1f ms; refined inverses %d (worst residual %.1e, fp64 again %d)\n",
-                   lev, nb, HL.ncolours, L->cur.size(), (long long)sum_a, (long long)sum_s,
-                   (long long)max_a, (long long)max_r, L->pool_size * 16.0 / 1e6, lms, ns_boxes,
-                   ns_worst, ns_fallback);
-    js << (first_level ? "" : ", ") << "{\"level\": " << lev << ", \"boxes\": " << nb
-       << ", \"colours\": " << HL.ncolours << ", \"n_proxy\": " << nprox
-       << ", \"current\": " << L->cur.size()
-       << ", \"sum_a\": " << sum_a << ", \"sum_s\": " << sum_s << ", \"max_a\": " << max_a
-       << ", \"max_r\": " << max_r << ", \"refined_inverses\": " << ns_boxes
-       << ", \"refine_fallbacks\": " << ns_fallback << ", \"ms\": " << lms << "}";
-    first_level = false;
+    CK(cudaEventRecord(lev_t1[lev & 1].e, st));
+    pend.on = true;
+    pend.lev = lev;
+    pend.nb = nb;
+    pend.colours = HL.ncolours;
+    pend.nprox = nprox;
+    pend.ns_rmax = ns_rmax;
+    pend.current = L->cur.size();
+    pend.sum_a = sum_a;
+    pend.sum_s = sum_s;
+    pend.max_a = max_a;
+    pend.max_r = max_r;
+    pend.pool = L->pool_size;
+    pend.r.resize((size_t)nb);
+    for (int e = 0; e < nb; ++e) pend.r[(size_t)e] = run[(size_t)e].r;
     prev = std::move(L);
   }
+  stream_wait(st);
+  finish_pending();
   // ---- root ----------------------------------------------------------------
   Timer rt;
   std::unique_ptr<LevelState> R;

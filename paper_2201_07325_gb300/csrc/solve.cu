@@ -161,7 +161,7 @@ __device__ __forceinline__ void mv_dots(const double2* __restrict__ M, int64_t l
 // outputs (16 or 32 per tile); when fewer than 256 outputs are left, the
 // remaining threads split q into interleaved groups whose sums meet in red
 // (256 entries per right-hand side, summed in a fixed group order).
-// store(o, y) receives the NR results of output o.
+// store(o, cc, y) receives the result of output o for right-hand side cc.
 template <int NR, bool kCj, class Store>
 __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t ld,
                                          const float4* X, int xs, int no, int nq, float4* red,
@@ -193,13 +193,10 @@ __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t 
       }
       if (q < nq) apply(Mo[(int64_t)q * ld], q);
     }
-    double2 y[NR];
     if (qg == 1) {
-      if (o < no) {
+      if (o < no)
 #pragma unroll
-        for (int cc = 0; cc < NR; ++cc) y[cc] = make_double2(df_value(ar[cc]), df_value(ai[cc]));
-        store(o, y);
-      }
+        for (int cc = 0; cc < NR; ++cc) store(o, cc, make_double2(df_value(ar[cc]), df_value(ai[cc])));
     } else {
 #pragma unroll
       for (int cc = 0; cc < NR; ++cc)
@@ -214,9 +211,8 @@ __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t 
             sr = df_add(sr, DF{w.x, w.y});
             si = df_add(si, DF{w.z, w.w});
           }
-          y[cc] = make_double2(df_value(sr), df_value(si));
+          store(o, cc, make_double2(df_value(sr), df_value(si)));
         }
-        store(o, y);
       }
       __syncthreads();
     }
@@ -254,13 +250,11 @@ __device__ __forceinline__ void mvr_dots(const double2* __restrict__ M, int64_t 
       }
       if (q < nq) apply(Mo[q], q);
     }
-    double2 y[NR];
 #pragma unroll
     for (int cc = 0; cc < NR; ++cc) {
       const DF sr = df_group_sum(ar[cc], sw), si = df_group_sum(ai[cc], sw);
-      y[cc] = make_double2(df_value(sr), df_value(si));
+      if (sl == 0 && o < no) store(o, cc, make_double2(df_value(sr), df_value(si)));
     }
-    if (sl == 0 && o < no) store(o, y);
   }
 }
 
@@ -274,18 +268,12 @@ __device__ __forceinline__ void stage_rhs(float4* X, int cnt, int cb, int nrhs, 
   }
 }
 
-// v[c][dof] -= y[cc] for the group's right-hand sides (all old values are
-// read before any is written back)
-template <int NR>
-__device__ __forceinline__ void sub_rhs(double2* v, int64_t n, int cb, int nrhs, int dof,
-                                        const double2* y) {
-  double2 old[NR];
-#pragma unroll
-  for (int cc = 0; cc < NR; ++cc)
-    if (cb + cc < nrhs) old[cc] = v[(int64_t)(cb + cc) * n + dof];
-#pragma unroll
-  for (int cc = 0; cc < NR; ++cc)
-    if (cb + cc < nrhs) v[(int64_t)(cb + cc) * n + dof] = csub(old[cc], y[cc]);
+// v[cb + cc][dof] -= y (a right-hand side of the group)
+__device__ __forceinline__ void sub_rhs(double2* v, int64_t n, int cb, int cc, int nrhs, int dof,
+                                        double2 y) {
+  if (cb + cc >= nrhs) return;
+  double2* p = v + (int64_t)(cb + cc) * n + dof;
+  *p = csub(*p, y);
 }
 
 // forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
@@ -304,7 +292,7 @@ __global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes
   __syncthreads();
   const int kc = it.c1 - it.c0;
   const int* Ridx = B.idx + it.c0;
-  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Ridx[o], y); };
+  auto st = [=](int o, int cc, double2 y) { sub_rhs(v, n, cb, cc, nrhs, Ridx[o], y); };
   const double2* M = B.T + (int64_t)it.c0 * B.ldT;
   if (adjoint) mvr_dots<NR, true>(M, B.ldT, X, B.s, kc, B.s, st);
   else mvr_dots<NR, false>(M, B.ldT, X, B.s, kc, B.s, st);
@@ -334,10 +322,8 @@ __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes
   stage_rhs<NR>(Y, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
   double2* zo = zbuf + B.zoff + it.c0;
-  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Y, red, adjoint != 0, [=](int o, const double2* z) {
-#pragma unroll
-    for (int cc = 0; cc < NR; ++cc)
-      if (cb + cc < nrhs) zo[(int64_t)(cb + cc) * zstride + o] = z[cc];
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Y, red, adjoint != 0, [=](int o, int cc, double2 z) {
+    if (cb + cc < nrhs) zo[(int64_t)(cb + cc) * zstride + o] = z;
   });
 }
 
@@ -358,8 +344,8 @@ __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxe
                 [&](int c, int k) { return partial[(int64_t)c * pstride + B.toff + k]; });
   __syncthreads();
   const int* Ridx = B.idx + it.c0;
-  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Tt, red, adjoint != 0, [=](int o, const double2* y) {
-    sub_rhs<NR>(v, n, cb, nrhs, Ridx[o], y);
+  xinv_rows<NR>(B, it.c0, it.c1 - it.c0, Tt, red, adjoint != 0, [=](int o, int cc, double2 y) {
+    sub_rhs(v, n, cb, cc, nrhs, Ridx[o], y);
   });
 }
 
@@ -378,7 +364,7 @@ __global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxe
   stage_rhs<NR>(Xr, B.r, cb, nrhs, [&](int c, int k) { return v[(int64_t)c * n + B.idx[k]]; });
   __syncthreads();
   const int* Sidx = B.idx + B.r + it.c0;
-  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Sidx[o], y); };
+  auto st = [=](int o, int cc, double2 y) { sub_rhs(v, n, cb, cc, nrhs, Sidx[o], y); };
   if (adjoint) mvr_cols<NR, true>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
   else mvr_cols<NR, false>(B.T + it.c0, B.ldT, Xr, B.r, it.c1 - it.c0, B.r, red, st);
 }
@@ -404,7 +390,7 @@ __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxe
   });
   __syncthreads();
   const int* Cidx = B.idx + r + it.c0;
-  auto st = [=](int o, const double2* y) { sub_rhs<NR>(v, n, cb, nrhs, Cidx[o], y); };
+  auto st = [=](int o, int cc, double2 y) { sub_rhs(v, n, cb, cc, nrhs, Cidx[o], y); };
   const int w = it.c1 - it.c0;
   if (!adjoint) mvr_cols<NR, false>(B.XCR + it.c0, B.ldL, Z, r, w, r, red, st);
   else mvr_dots<NR, true>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, Z, r, w, r, st);
@@ -433,10 +419,8 @@ __global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxe
   stage_rhs<NR>(U, w, cb, nrhs,
                 [&](int c, int j) { return v[(int64_t)c * n + Cidx[it.c0 + j]]; });
   __syncthreads();
-  auto st = [=](int o, const double2* y) {
-#pragma unroll
-    for (int cc = 0; cc < NR; ++cc)
-      if (cb + cc < nrhs) partial[(int64_t)(cb + cc) * pstride + it.part + o] = y[cc];
+  auto st = [=](int o, int cc, double2 y) {
+    if (cb + cc < nrhs) partial[(int64_t)(cb + cc) * pstride + it.part + o] = y;
   };
   if (!adjoint) mvr_cols<NR, false>(B.XRC + (int64_t)it.c0 * B.ldU, B.ldU, U, w, r, w, red, st);
   else mvr_dots<NR, true>(B.XCR + it.c0, B.ldL, U, w, r, w, st);
