@@ -112,12 +112,15 @@ typedef struct fmmlu_opts {
                                  either way). Default FMMLU_ID_AUTO.        */
   double xrr_refine_tol;      /* schur_emulation 1 only: X_RR^{-1} of boxes
                                  with 32 <= r <= 640 is an fp32 inverse plus
-                                 three Newton-Schulz steps on the tensor
-                                 cores; a box whose last residual
-                                 max|I - X_RR X| exceeds this tolerance is
-                                 inverted again in fp64. Default 1e-9; 0
-                                 inverts every such box again; < 0 turns the
-                                 refinement off (fp64 Gauss-Jordan).        */
+                                 two or three Newton-Schulz steps on the
+                                 tensor cores (the third is skipped where
+                                 the second step's residual e gives
+                                 (r e)^2 <= min(tol, eps/100)); a box whose
+                                 last residual max|I - X_RR X| exceeds this
+                                 tolerance is inverted again in fp64.
+                                 Default 1e-9; 0 inverts every such box
+                                 again; < 0 turns the refinement off (fp64
+                                 Gauss-Jordan).                             */
   int solve_chunk;            /* rows of X_CR (forward sweep) and columns of
                                  X_RC (backward sweep) per CTA in the solves:
                                  0 (default) = chosen by the tuner when

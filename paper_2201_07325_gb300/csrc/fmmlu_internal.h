@@ -108,6 +108,7 @@ struct LevelDev {   // device state of a level
   const int64_t* ns_off;
   unsigned long long* ns_err;   // max |I - X_RR X_1| per box, as double bits
   int ns_rmax;
+  const unsigned char* ns_skip = nullptr;   // per box: skip this refinement step
   // root block elimination on the tensor cores (one step: block [i0, i0 + r))
   double2* root_A;   // n0 x n0, ld n0
   double2* root_W;   // later x r, ld later
@@ -305,6 +306,11 @@ cudaError_t launch_gj32(const LevelDev& L, int b0, const TcUnit* d_units, int nu
 // inverted again in fp64 from the stored copy of X_RR (one CTA per box)
 void launch_ns_fallback(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, int amax,
                         double thr, cudaStream_t st);
+// flags the refined boxes whose first residual e already bounds the next
+// iterate's by (r e)^2 <= thr, so that a third step can skip them (skip[b]
+// = 1), and clears their residual record
+void launch_ns_flag(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, double thr,
+                    unsigned char* skip, cudaStream_t st);
 // gj_dist.cu: X_RR^{-1} of one box over P cooperating CTAs (cooperative launch)
 size_t gj_dist_scratch_bytes(int a);
 int gj_dist_capacity(int amax);

@@ -552,6 +552,26 @@ __global__ void __launch_bounds__(512) k_ns_fallback(LevelDev L, int b0,
   gauss_jordan(X, r, d.a, ipiv, L.status);
 }
 
+__global__ void k_ns_flag(LevelDev L, int b0, const TcUnit* __restrict__ units, int nunits,
+                          double thr, unsigned char* skip) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nunits) return;
+  const int b = b0 + units[u].box;
+  const double r = (double)L.run[b].r;
+  const double e = __longlong_as_double((long long)L.ns_err[b]);
+  const double bound = (r * e) * (r * e);
+  const bool done = bound <= thr;   // false for NaN
+  skip[b] = done ? 1 : 0;
+  if (done) L.ns_err[b] = 0ull;     // the fallback test passes on the bound
+}
+
+void launch_ns_flag(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, double thr,
+                    unsigned char* skip, cudaStream_t st) {
+  if (nunits <= 0) return;
+  FMMLU_LAUNCH("xrr_fallback", st,
+               k_ns_flag<<<(nunits + 127) / 128, 128, 0, st>>>(L, b0, d_units, nunits, thr, skip));
+}
+
 void launch_ns_fallback(const LevelDev& L, int b0, const TcUnit* d_units, int nunits, int amax,
                         double thr, cudaStream_t st) {
   if (nunits <= 0) return;

@@ -321,14 +321,15 @@ struct TcXrr {      // X_RR = A_RR - A_RS T (before inversion): r x r x s
 // Newton-Schulz refinement of X ~ X_RR^{-1} (boxes kNsMin <= r <= ns_rmax):
 // Y = X_RR X into the box's product scratch (recording max |I - Y|), then
 // X <- 2 X - X Y in place (the operands were split before the product runs).
-__device__ __forceinline__ bool ns_box(const LevelDev& L, const BoxRun& rr) {
-  return rr.r >= kNsMin && rr.r <= L.ns_rmax;
+__device__ __forceinline__ bool ns_box(const LevelDev& L, const BoxDesc& d, const BoxRun& rr) {
+  if (rr.r < kNsMin || rr.r > L.ns_rmax) return false;
+  return !(L.ns_skip && L.ns_skip[&d - L.desc]);   // a step the box no longer needs
 }
 struct TcNsY {
   static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
-  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+  __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, rr);
+    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, d, rr);
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
     const int b = (int)(&d - L.desc);
@@ -348,9 +349,9 @@ struct TcNsY {
 };
 struct TcNsX {
   static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
-  __device__ static bool dims(const LevelDev& L, const BoxDesc&, const BoxRun& rr, int& m, int& n,
+  __device__ static bool dims(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int& m, int& n,
                               int& k) {
-    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, rr);
+    m = rr.r; n = rr.r; k = rr.r; return ns_box(L, d, rr);
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
     return L.arena[d.Xinv_off + i + (int64_t)kk * d.a];
