@@ -16,6 +16,7 @@
 //  * k_assemble_root -- the remaining dense block A_{B_t B_t}.
 //  * k_matvec        -- dense on-the-fly A v (independent of the factorization).
 #include "device_common.cuh"
+#include "dfloat.cuh"
 
 namespace fmmlu {
 
@@ -123,6 +124,14 @@ constexpr int kIdRows = 64;   // most half-rows per block (pairs of rows)
 // computed once, before the entries. In single precision (C = float2) the
 // kernel is evaluated from the split fp32 geometry and the Schur updates are
 // added in fp32; in double precision everything is fp64.
+// a Schur update added to an ID-matrix entry: complex64 entries take it
+// narrowed from its bit pattern (the high and low fp32 parts, summed)
+__device__ __forceinline__ double2 id_delta(double2 v, double2) { return v; }
+__device__ __forceinline__ float2 id_delta(double2 v, float2) {
+  const DF x = df_split_bits(v.x), y = df_split_bits(v.y);
+  return make_float2(x.h + x.l, y.h + y.l);
+}
+
 template <typename C>
 __global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
   using R = decltype(C().x);
@@ -189,10 +198,10 @@ __global__ void k_assemble_id(LevelDev L, Geometry g, int b0, int rpb) {
       const int64_t off_o = L.qpair[d.qpair + 2 * qloc[i]];
       if (off_o >= 0) {
         const int ldc = L.cur_a0[L.qlist[d.qbeg + qloc[i]]];
-        o = cadd(o, from_d2<C>(L.delta[off_o + qpos[i] + (int64_t)j * ldc]));
+        o = cadd(o, id_delta(L.delta[off_o + qpos[i] + (int64_t)j * ldc], C()));
       }
       const int64_t off_i = L.qpair[d.qpair + 2 * qloc[i] + 1];
-      if (off_i >= 0) tr = cadd(tr, from_d2<C>(L.delta[off_i + j + (int64_t)qpos[i] * a]));
+      if (off_i >= 0) tr = cadd(tr, id_delta(L.delta[off_i + j + (int64_t)qpos[i] * a], C()));
       v_out = o;
       v_in = tr;
       r_out = i;
@@ -318,8 +327,10 @@ __global__ void __launch_bounds__(256) k_assemble_elim(LevelDev L, Geometry g, i
       if (kF && r.dof != c.dof) {
         float2 fa, fb;
         entry_pair_f(g.f, kf, ef, r.dof, c.dof, fa, fb);
-        arc = to_d2(fa);
-        acr = to_d2(fb);
+        // widened from the bit patterns: the conversion instruction would
+        // occupy GB300's narrow fp64 pipe
+        arc = make_double2(f2d_bits(fa.x), f2d_bits(fa.y));
+        acr = make_double2(f2d_bits(fb.x), f2d_bits(fb.y));
       } else {
         entry_pair(g, r.dof, c.dof, arc, acr);
       }

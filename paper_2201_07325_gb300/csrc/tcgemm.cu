@@ -35,6 +35,7 @@
 #include <mutex>
 
 #include "device_common.cuh"
+#include "dfloat.cuh"
 
 namespace fmmlu {
 
@@ -473,6 +474,14 @@ struct TcSvT {
   }
 };
 
+// an ID-matrix entry as complex128: complex64 entries are widened from their
+// bit patterns (integer operations; the conversion instruction would run on
+// GB300's narrow fp64 pipe, which it saturated in the split passes)
+__device__ __forceinline__ double2 id_entry(double2 v) { return v; }
+__device__ __forceinline__ double2 id_entry(float2 v) {
+  return make_double2(f2d_bits(v.x), f2d_bits(v.y));
+}
+
 // G = M^H M of the ID matrix M (m x a, column-major, ld mmax): a x a x m
 template <typename CM>
 struct TcGram {
@@ -482,10 +491,10 @@ struct TcGram {
     m = d.a; n = d.a; k = 2 * rr.nq + 2 * L.n_proxy; return d.a > 0;
   }
   __device__ static double2 A(const LevelDev& L, const BoxDesc& d, const BoxRun&, int i, int kk) {
-    return to_d2(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)i * d.mmax]);
+    return id_entry(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)i * d.mmax]);
   }
   __device__ static double2 B(const LevelDev& L, const BoxDesc& d, const BoxRun&, int kk, int j) {
-    return to_d2(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)j * d.mmax]);
+    return id_entry(reinterpret_cast<const CM*>(L.Mbuf)[d.M_off + kk + (int64_t)j * d.mmax]);
   }
   __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun&, const TcExtra& x,
                              int i, int j, double vr, double vi) {
