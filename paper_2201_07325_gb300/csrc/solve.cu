@@ -278,7 +278,7 @@ __device__ __forceinline__ void sub_rhs(double2* v, int64_t n, int cb, int cc, i
 
 // forward: b_R[k] -= sum_i op(T)(i, k) b_S[i] for the chunk's rows k
 template <int NR>
-__global__ void __launch_bounds__(256) k_sw_y(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_sw_y(const SolveBox* __restrict__ boxes,
                                               const SweepItem* __restrict__ items, int i0,
                                               double2* __restrict__ v, int64_t n, int nrhs,
                                               int adjoint) {
@@ -308,7 +308,7 @@ __device__ __forceinline__ void xinv_rows(const SolveBox& B, int c0, int kc, con
 
 // forward: z = op(X_RR^{-1}) b_R for the chunk's rows, into the box's scratch
 template <int NR>
-__global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_sw_z(const SolveBox* __restrict__ boxes,
                                               const SweepItem* __restrict__ items, int i0,
                                               const double2* __restrict__ v, int64_t n,
                                               double2* __restrict__ zbuf, int64_t zstride,
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) k_sw_z(const SolveBox* __restrict__ boxes
 
 // backward: x_R[k] -= sum_l op(X_RR^{-1})(k, l) t[l], t = the summed partials
 template <int NR>
-__global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_sw_xr(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
                                                const double2* __restrict__ partial,
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) k_sw_xr(const SolveBox* __restrict__ boxe
 
 // backward: x_S[i] -= sum_k op(T)(i, k) x_R[k] for the chunk's rows i
 template <int NR>
-__global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_sw_xs(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n, int nrhs,
                                                int adjoint) {
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) k_sw_xs(const SolveBox* __restrict__ boxe
 
 // forward: b_C -= op(X_CR) z on the chunk's rows of C
 template <int NR>
-__global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_fwd_c(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                double2* __restrict__ v, int64_t n,
                                                const double2* __restrict__ zbuf, int64_t zstride,
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) k_fwd_c(const SolveBox* __restrict__ boxe
 // and right-hand-side group, reset by that CTA; no CTA waits) sums the box's
 // partials in chunk order into its t slots
 template <int NR>
-__global__ void __launch_bounds__(256) k_bwd_t(const SolveBox* __restrict__ boxes,
+__global__ void __launch_bounds__(256, 4) k_bwd_t(const SolveBox* __restrict__ boxes,
                                                const SweepItem* __restrict__ items, int i0,
                                                const double2* __restrict__ v, int64_t n,
                                                double2* __restrict__ partial, int64_t pstride,
