@@ -172,6 +172,35 @@ struct ScratchPool {
   }
 };
 
+// Device buffers in numbered slots, grown (never shrunk) on demand: the
+// Schur pools of the levels alternate between two slots, so a factorization
+// allocates a pool only when a level needs more than its slot holds and
+// frees them all at its end (a cudaFree waits for the device).
+struct DevSlots {
+  std::vector<std::pair<void*, size_t>> slots;
+  template <typename T>
+  T* get(int slot, size_t count) {
+    if ((int)slots.size() <= slot) slots.resize((size_t)slot + 1, {nullptr, 0});
+    auto& sl = slots[(size_t)slot];
+    const size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+    if (sl.second < bytes) {
+      if (sl.first) {
+        HostTimer t(&HostTimes::release);
+        cudaFree(sl.first);
+      }
+      sl.first = nullptr;
+      sl.second = 0;
+      sl.first = dalloc<unsigned char>(bytes);
+      sl.second = bytes;
+    }
+    return static_cast<T*>(sl.first);
+  }
+  ~DevSlots() {
+    for (auto& sl : slots)
+      if (sl.first) cudaFree(sl.first);
+  }
+};
+
 // Pinned host buffers in numbered slots, grown (never shrunk) on demand.
 struct PinnedPool {
   std::vector<std::pair<void*, size_t>> slots;
@@ -484,7 +513,7 @@ struct LevelState {
 };
 
 std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const LevelState* prev,
-                                       const HLevel* lists, cudaStream_t st) {
+                                       const HLevel* lists, cudaStream_t st, DevSlots* pools) {
   auto L = std::make_unique<LevelState>();
   L->level = level;
   L->cur = current_boxes(T, level);
@@ -601,7 +630,7 @@ std::unique_ptr<LevelState> make_level(const TreeHost& T, int level, const Level
       tot += (int64_t)L->a0[x] * L->a0[P.ys[e]];
     }
   L->pool_size = tot;
-  L->d_pool = L->mem.get<double2>((size_t)tot);
+  L->d_pool = pools ? pools->get<double2>(level & 1, (size_t)tot) : L->mem.get<double2>((size_t)tot);
   if (tot) CK(cudaMemsetAsync(L->d_pool, 0, (size_t)tot * sizeof(double2), st));
   L->d_cur_n = L->mem.up(L->cur_n, st);
   L->d_cur_off = L->mem.up(L->off, st);
@@ -937,6 +966,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   // status word and refinement residuals (read one level later, once the
   // GPU has finished the level).
   PinnedPool pinned;
+  DevSlots pools;   // the levels' Schur pools, by level parity
   enum { kPinRun = 0, kPinCurN = 1, kPinActPos = 2, kPinStatus = 3, kPinNs = 4, kPinStatusIds = 5 };
   Ev ev_ids_holder;   // the last colour's IDs of a level are final
   CK(cudaEventCreateWithFlags(&ev_ids_holder.e, cudaEventDisableTiming));
@@ -1018,7 +1048,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
     std::unique_ptr<LevelState> L;
     {
       HostTimer mt(&HostTimes::make_level);
-      L = make_level(T, lev, prev.get(), &HL, st);
+      L = make_level(T, lev, prev.get(), &HL, st, &pools);
     }
     const auto setup0 = std::chrono::steady_clock::now();
     auto sub0 = setup0;
@@ -1778,7 +1808,7 @@ void factor_impl(const fmmlu_tree* tree, const double* pts, const double* nrm, c
   } else {
     {
       HostTimer mt(&HostTimes::make_level);
-      R = make_level(T, root_level, prev.get(), nullptr, st);
+      R = make_level(T, root_level, prev.get(), nullptr, st, &pools);
     }
     stream_wait(st);
     prev.reset();

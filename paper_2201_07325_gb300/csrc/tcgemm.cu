@@ -33,6 +33,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "dfloat.cuh"
@@ -240,7 +241,45 @@ struct TcSchur {    // Delta(S|N, S|N) -= W X_RC: (s+n) x (s+n) x r
     const double2 c = *pz;
     *pz = make_double2(c.x - vr, c.y - vi);
   }
+  // The same update split into a per-row part, computed once for a row's 16
+  // outputs, and a per-column part; the index arrays are read through the
+  // read-only path (nothing writes them during the product), so the
+  // compiler may keep and reorder those loads across the pool stores.
+  struct Row {
+    const int* perm;
+    const int* npos;
+    const int* nloc;
+    int64_t prow;   // pairtab entry of (row's owner, 0)
+    int s, xp, ld;
+  };
+  __device__ static Row row(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i) {
+    Row w;
+    w.s = rr.s;
+    w.perm = L.iarena + d.idx_off + d.a + d.nmax;
+    const int* ndof = L.rows + d.rows_off + 3 * d.qmax;
+    w.npos = ndof + d.nmax;
+    w.nloc = w.npos + d.nmax;
+    const int xl = i < w.s ? 0 : __ldg(w.nloc + i - w.s);
+    w.xp = i < w.s ? __ldg(w.perm + i) : __ldg(w.npos + i - w.s);
+    w.prow = d.pairtab + (int64_t)xl * (1 + d.ncnt);
+    w.ld = xl == 0 ? d.a : __ldg(L.cur_a0 + __ldg(L.nlist + d.nbeg + xl - 1));
+    return w;
+  }
+  __device__ static void col(const LevelDev& L, const Row& w, int j, double vr, double vi) {
+    const int yl = j < w.s ? 0 : __ldg(w.nloc + j - w.s);
+    const int yp = j < w.s ? __ldg(w.perm + j) : __ldg(w.npos + j - w.s);
+    const int64_t off = __ldg(L.pairtab + w.prow + yl);
+    if (off < 0) { set_status(L.status, kStatusBound); return; }
+    double2* pz = L.delta + off + w.xp + (int64_t)yp * w.ld;
+    const double2 c = *pz;
+    *pz = make_double2(c.x - vr, c.y - vi);
+  }
 };
+
+struct TcNoRow { struct Row {}; };
+template <class Prob, class = void> struct TcRowEpi { static constexpr bool value = false; };
+template <class Prob>
+struct TcRowEpi<Prob, std::void_t<typename Prob::Row>> { static constexpr bool value = true; };
 
 struct TcW {        // W = X_CR X_RR^{-1}: (s+n) x r x r, stored
   static constexpr bool kConj = false, kUpper = false, kAk = false, kBk = true;
@@ -958,6 +997,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const BoxDesc& d = L.desc[T.b];
         const BoxRun rr = L.run[T.b];
         const int ei = expo[t.ea_off + i];
+        [[maybe_unused]] typename std::conditional<TcRowEpi<Prob>::value, Prob, TcNoRow>::type::Row
+            w;
+        if constexpr (TcRowEpi<Prob>::value) w = Prob::row(L, d, rr, i);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = T.j0 + 16 * half + c;
@@ -976,7 +1018,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
             vr = ldexp((double)xh[c][0], E - 32) + ldexp((double)xl[c][0], E - 16 - 8 * DMAX);
             vi = ldexp((double)xh[c][1], E - 32) + ldexp((double)xl[c][1], E - 16 - 8 * DMAX);
           }
-          Prob::epi(L, d, rr, x, i, j, vr, vi);
+          if constexpr (TcRowEpi<Prob>::value) Prob::col(L, w, j, vr, vi);
+          else Prob::epi(L, d, rr, x, i, j, vr, vi);
         }
       }
     }
