@@ -317,6 +317,19 @@ struct TcG1 {       // G1[s:a, :] -= T^T G1[0:s, :]: r x (a+n) x s
     const double2 t = *c;
     *c = make_double2(t.x - vr, t.y - vi);
   }
+  // per-row part of the update (the row's base and stride), once per 16 outputs
+  struct Row {
+    double2* base;
+    int64_t ld;
+  };
+  __device__ static Row row(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i) {
+    return Row{L.arena + d.G1_off + (rr.s + i), (int64_t)d.a};
+  }
+  __device__ static void col(const LevelDev&, const Row& w, int j, double vr, double vi) {
+    double2* c = w.base + (int64_t)j * w.ld;
+    const double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
 };
 
 struct TcG3 {       // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
@@ -334,6 +347,20 @@ struct TcG3 {       // G3[:, s:a] -= G3[:, 0:s] T: (a+n) x r x s
   __device__ static void epi(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, const TcExtra&,
                              int i, int j, double vr, double vi) {
     double2* c = L.arena + d.G3_off + i + (int64_t)(rr.s + j) * (d.a + d.nmax);
+    const double2 t = *c;
+    *c = make_double2(t.x - vr, t.y - vi);
+  }
+  // per-row part of the update (the row's base and stride), once per 16 outputs
+  struct Row {
+    double2* base;
+    int64_t ld;
+  };
+  __device__ static Row row(const LevelDev& L, const BoxDesc& d, const BoxRun& rr, int i) {
+    const int64_t ld = d.a + d.nmax;
+    return Row{L.arena + d.G3_off + i + (int64_t)rr.s * ld, ld};
+  }
+  __device__ static void col(const LevelDev&, const Row& w, int j, double vr, double vi) {
+    double2* c = w.base + (int64_t)j * w.ld;
     const double2 t = *c;
     *c = make_double2(t.x - vr, t.y - vi);
   }
