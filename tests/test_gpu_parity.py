@@ -457,11 +457,12 @@ def test_invalid_arguments(pkg):
 
 
 @pytest.mark.parametrize("eps", [1e-6, 1e-14])
-def test_tensor_core_sweeps_equal_fp64_sweeps(pkg, ell, eps):
-    """With 16 right-hand sides the products with the C blocks of the sweeps
-    run on the tensor cores (exact split); they must agree with the fp64
-    sweeps to rounding, solve and adjoint, eager and replayed as a graph,
-    and at eps -> 0 reproduce the dense solve."""
+def test_tensor_core_sweeps_equal_double_float_sweeps(pkg, ell, eps):
+    """With 16 right-hand sides and solve_tc_nrhs = 8 the products with the C
+    blocks of the sweeps run on the tensor cores (exact split); they must
+    agree with the double-float sweeps (solve_tc_nrhs = 0) to rounding, solve
+    and adjoint, eager and replayed as a graph, and at eps -> 0 reproduce the
+    dense solve."""
     s, A, b, xd = ell
     rng = np.random.default_rng(16)
     Bm = rng.standard_normal((16, s.n)) + 1j * rng.standard_normal((16, s.n))
