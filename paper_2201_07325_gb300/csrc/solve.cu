@@ -221,13 +221,16 @@ __device__ __forceinline__ void mvr_cols(const double2* __restrict__ M, int64_t 
 
 // y[o][cc] = sum_{q < nq} op(M[q + o ld]) X[cc][q], o < no: every output is a
 // dot product along a contiguous column, taken by a group of 4 to 32 lanes
-// (sized so that every lane takes at least four terms) and summed across
-// the group with shuffles.
+// and summed across the group with shuffles. The group is as small as still
+// fills the CTA's 256 threads (each halving saves a shuffle round for all NR
+// right-hand sides) and at most a quarter of nq (four terms per lane).
 template <int NR, bool kCj, class Store>
 __device__ __forceinline__ void mvr_dots(const double2* __restrict__ M, int64_t ld,
                                          const float4* X, int xs, int no, int nq, Store store) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int sw = nq >= 128 ? 32 : (nq >= 64 ? 16 : (nq >= 32 ? 8 : 4));
+  int sw = 32;
+  while (sw > 4 && (sw / 2) * no >= (int)blockDim.x) sw >>= 1;
+  while (sw > 4 && nq < 4 * sw) sw >>= 1;
   const int per = 32 / sw;
   const int sl = lane % sw, sub = lane / sw;
   for (int ob = w * per; ob < no; ob += nw * per) {
