@@ -88,9 +88,6 @@ __device__ __forceinline__ float4 cdf_split_bits(double2 v) {
   const DF r = df_split_bits(v.x), i = df_split_bits(v.y);
   return make_float4(r.h, r.l, i.h, i.l);
 }
-__device__ __forceinline__ double2 cdf_value(float4 v) {
-  return make_double2(df_value(DF{v.x, v.y}), df_value(DF{v.z, v.w}));
-}
 
 // (re, im) += op(m) x, op = conj when kCj
 template <bool kCj>
