@@ -151,13 +151,13 @@ def measured_peaks() -> dict:
 # translation unit (and its local headers) of each kernel class whose DRAM
 # counters are recorded
 _COMMON = ("device_common.cuh", "fmmlu_internal.h")
-_KERNEL_FILES = {name: ("tcgemm.cu",) + _COMMON
+_KERNEL_FILES = {name: ("tcgemm.cu", "dfloat.cuh") + _COMMON
                  for name in ("schur_tc", "gram", "gemm_g1_tc", "gemm_g3_tc", "gemm_w_tc",
                               "gemm_xrr_tc", "ns_tc", "root_w_tc", "root_schur_tc", "tc_split")}
 _KERNEL_FILES.update({"pchol": ("pchol.cu", "coop.cuh") + _COMMON,
                       "xrr_inverse32": ("gj_dist.cu", "coop.cuh") + _COMMON,
-                      "assemble_id": ("assembly.cu",) + _COMMON,
-                      "assemble_elim": ("assembly.cu",) + _COMMON})
+                      "assemble_id": ("assembly.cu", "dfloat.cuh") + _COMMON,
+                      "assemble_elim": ("assembly.cu", "dfloat.cuh") + _COMMON})
 
 
 def kernel_source_hash(kernel: str | None = None) -> str:
