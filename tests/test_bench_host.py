@@ -14,7 +14,7 @@ import bench  # noqa: E402
 def _fake_tree(tmp_path):
     csrc = tmp_path / "paper_2201_07325_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("tcgemm.cu", "device_common.cuh", "fmmlu_internal.h", "solve.cu"):
+    for f in ("tcgemm.cu", "dfloat.cuh", "device_common.cuh", "fmmlu_internal.h", "solve.cu"):
         (csrc / f).write_text(f"// {f}\n")
     (tmp_path / "profiles").mkdir()
     return csrc
@@ -32,10 +32,13 @@ def test_recorded_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     (csrc / "solve.cu").write_text("// changed\n")
     assert bench.kernel_source_hash("schur_tc") == h
     assert bench.recorded_traffic("schur_tc", "ellipsoid50k") == 123
-    # a change inside it drops them
-    (csrc / "tcgemm.cu").write_text("// changed\n")
-    assert bench.kernel_source_hash("schur_tc") != h
+    # a change inside it (a header it includes counts) drops them
+    (csrc / "dfloat.cuh").write_text("// changed\n")
+    h2 = bench.kernel_source_hash("schur_tc")
+    assert h2 != h
     assert bench.recorded_traffic("schur_tc", "ellipsoid50k") is None
+    (csrc / "tcgemm.cu").write_text("// changed\n")
+    assert bench.kernel_source_hash("schur_tc") not in (h, h2)
 
 
 def test_unlisted_kernels_hash_all_sources(tmp_path, monkeypatch):
